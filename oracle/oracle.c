@@ -1,0 +1,374 @@
+/*
+ * CPU oracle for the MG-sketch local-moving sweep (arXiv 2411.02268).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded
+ * restatement of what the method computes.  It shares no code with the CUDA
+ * path; only the tests, the smoke check and the benchmark's CPU-baseline leg
+ * may load it.
+ *
+ * All arithmetic is exact integer arithmetic: weights are uint32, weighted
+ * degrees and community totals uint64, modularity gains signed 128-bit.
+ *
+ * Notation follows Section 3 of the paper:
+ *   K_i        weighted degree, sum of w over row i (self-loop entry included)
+ *   K_{i->c}   sum of w over entries (i, j) of row i with j != i and C_j = c
+ *   Sigma_c    sum of K_i over members of c
+ *   sigma_c    sum of w over entries (i, j) with C_i = C_j = c
+ *   2m         sum of K_i over all vertices
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+#define EMPTY_KEY 0xFFFFFFFFu
+
+enum { MODE_LOUVAIN = 0, MODE_LPA = 1, MODE_REFINE = 2 };
+
+/* ---------------------------------------------------------------------------
+ * Weighted degree and community totals (Section 3).
+ * ------------------------------------------------------------------------- */
+void or_degrees(int64_t n, const int64_t* off, const uint32_t* w, uint64_t* K) {
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t s = 0;
+        for (int64_t e = off[i]; e < off[i + 1]; ++e) s += w[e];
+        K[i] = s;
+    }
+}
+
+void or_community_totals(int64_t n, const uint32_t* labels, const uint64_t* K,
+                         uint64_t* Sigma, uint32_t* size) {
+    memset(Sigma, 0, sizeof(uint64_t) * (size_t)n);
+    memset(size, 0, sizeof(uint32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        Sigma[labels[i]] += K[i];
+        size[labels[i]] += 1;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Modularity, Eq. 1:  Q = sum_c [ sigma_c/2m - (Sigma_c/2m)^2 ]
+ *                       = (2m * sum_c sigma_c - sum_c Sigma_c^2) / (2m)^2.
+ * Returns the integer parts: sum_c sigma_c, sum_c Sigma_c^2 (as two 64-bit
+ * halves) and 2m.  Labels must be < n.
+ * ------------------------------------------------------------------------- */
+void or_modularity_parts(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t* w,
+                         const uint32_t* labels, uint64_t* sigma_in, uint64_t* sq_lo,
+                         uint64_t* sq_hi, uint64_t* two_m) {
+    uint64_t* Sig = (uint64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(uint64_t));
+    uint64_t sin_ = 0, tm = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+            tm += w[e];
+            Sig[labels[i]] += w[e];
+            if (labels[cols[e]] == labels[i]) sin_ += w[e];
+        }
+    }
+    u128 sq = 0;
+    for (int64_t c = 0; c < n; ++c) sq += (u128)Sig[c] * (u128)Sig[c];
+    free(Sig);
+    *sigma_in = sin_;
+    *sq_lo = (uint64_t)sq;
+    *sq_hi = (uint64_t)(sq >> 64);
+    *two_m = tm;
+}
+
+/* ---------------------------------------------------------------------------
+ * Weighted Misra-Gries sketch, Algorithm 1 (Appendix A.1).
+ *
+ * keys[k], vals[k]; a slot with value 0 is empty.  The initial state is
+ * keys = EMPTY_KEY, vals = 0.  One update with community c and weight w:
+ *   1. add w to every slot whose key is c;
+ *   2. if some slot's key is c (live or zeroed), stop;
+ *   3. else put (c, w) into the empty slot with the largest index;
+ *   4. else subtract w from every slot, clamping at 0 (the new key is dropped).
+ * Unconditional variant (Section 4.1, "unconditional subtraction"): when c
+ * is not present, subtract w (clamped) from every slot first, then insert
+ * into the largest-index empty slot if one exists.
+ * ------------------------------------------------------------------------- */
+void or_sketch_update(uint32_t* keys, uint64_t* vals, int k, uint32_t c, uint64_t w, int uncond) {
+    int has = 0;
+    for (int p = 0; p < k; ++p) {
+        if (keys[p] == c) { vals[p] += w; has = 1; }
+    }
+    if (has) return;
+    if (uncond) {
+        for (int p = 0; p < k; ++p) vals[p] = vals[p] > w ? vals[p] - w : 0;
+    }
+    int e = -1;
+    for (int p = 0; p < k; ++p)
+        if (vals[p] == 0) e = p;
+    if (e >= 0) {
+        keys[e] = c;
+        vals[e] = w;
+    } else if (!uncond) {
+        for (int p = 0; p < k; ++p) vals[p] = vals[p] > w ? vals[p] - w : 0;
+    }
+}
+
+/* merge(A, B): every live slot of B, in slot order, is fed to A as one
+ * update.  (The paper streams one vertex per thread and needs no merge; the
+ * merge defines how partial sketches of one row are combined.) */
+void or_sketch_merge(uint32_t* akeys, uint64_t* avals, const uint32_t* bkeys, const uint64_t* bvals,
+                     int k, int uncond) {
+    for (int p = 0; p < k; ++p)
+        if (bvals[p] > 0) or_sketch_update(akeys, avals, k, bkeys[p], bvals[p], uncond);
+}
+
+/* ---------------------------------------------------------------------------
+ * Stream partition of a row.  A schedule maps the row length to a number of
+ * streams L (a power of two); entry e (global CSR index) of the row belongs
+ * to stream (e / V) mod L and each stream takes its entries in increasing e.
+ * The L partial sketches are combined by a tree: for o = L/2, L/4, ..., 1,
+ * S[s] = merge(S[s], S[s + o]) for every s < o; the result is S[0].
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int nbuckets;
+    const int64_t* deg_max; /* ascending; bucket b takes rows with length <= deg_max[b] */
+    const int32_t* lanes;   /* streams per row in bucket b */
+    int vec;                /* V */
+} or_sched;
+
+static int64_t streams_for(const or_sched* s, int64_t deg) {
+    for (int b = 0; b < s->nbuckets; ++b)
+        if (deg <= s->deg_max[b]) return s->lanes[b];
+    return s->lanes[s->nbuckets - 1];
+}
+
+/* Build the sketch of row i (self-loops skipped; in the refine mode only
+ * entries with bound[j] == bound[i] are taken, Algorithm 1 lines 2-3). */
+static void row_sketch(int64_t i, const int64_t* off, const int32_t* cols, const uint32_t* w,
+                       const uint32_t* labels, const uint32_t* bound, int k, int uncond,
+                       const or_sched* sched, uint32_t* keys_out, uint64_t* vals_out) {
+    int64_t deg = off[i + 1] - off[i];
+    int64_t L = streams_for(sched, deg);
+    int64_t V = sched->vec;
+    uint32_t* SK = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(L * k));
+    uint64_t* SV = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(L * k));
+    for (int64_t x = 0; x < L * k; ++x) { SK[x] = EMPTY_KEY; SV[x] = 0; }
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        int64_t j = cols[e];
+        if (j == i) continue;
+        if (bound && bound[j] != bound[i]) continue;
+        int64_t s = (e / V) % L;
+        or_sketch_update(SK + s * k, SV + s * k, k, labels[j], w[e], uncond);
+    }
+    for (int64_t o = L / 2; o >= 1; o /= 2)
+        for (int64_t s = 0; s < o; ++s)
+            or_sketch_merge(SK + s * k, SV + s * k, SK + (s + o) * k, SV + (s + o) * k, k, uncond);
+    memcpy(keys_out, SK, sizeof(uint32_t) * (size_t)k);
+    memcpy(vals_out, SV, sizeof(uint64_t) * (size_t)k);
+    free(SK);
+    free(SV);
+}
+
+/* Exact K_{i->c} by a second scan of row i (self-loops excluded). */
+static uint64_t link_weight(int64_t i, uint32_t c, const int64_t* off, const int32_t* cols,
+                            const uint32_t* w, const uint32_t* labels, const uint32_t* bound) {
+    uint64_t s = 0;
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        int64_t j = cols[e];
+        if (j == i) continue;
+        if (bound && bound[j] != bound[i]) continue;
+        if (labels[j] == c) s += w[e];
+    }
+    return s;
+}
+
+/* Scaled delta-modularity, Eq. 2 multiplied by 2m^2:
+ *   gain = 2m (K_{i->c} - K_{i->d}) - K_i (K_i + Sigma_c - Sigma_d). */
+static i128 dq_gain(uint64_t two_m, uint64_t Kic, uint64_t Kid, uint64_t Ki, uint64_t Sc, uint64_t Sd) {
+    return (i128)two_m * ((i128)Kic - (i128)Kid) - (i128)Ki * ((i128)Ki + (i128)Sc - (i128)Sd);
+}
+
+/* ---------------------------------------------------------------------------
+ * One synchronous sweep (every decision reads the sweep-start state).
+ *
+ * k > 0: candidates are the live keys of the row's MG sketch (value > 0),
+ *        exact K_{i->c} from a second scan (Section 4.1, Fig. 2).
+ * k = 0: exact: candidates are all distinct neighbour communities.
+ * The current community d is never a candidate; K_{i->d} is always exact.
+ *
+ * Louvain (and refine): gain as above; a singleton vertex may not join another
+ * singleton community with a larger id (stops pairwise swaps in a synchronous
+ * sweep); best gain wins, ties to the smaller id; moves iff gain > 0.
+ * LPA: largest K_{i->c} wins, ties to the smaller id; moves iff it exceeds
+ * K_{i->d}.  The refine mode restricts both scans to bound[j] == bound[i] and
+ * moves only vertices whose community is a singleton.
+ *
+ * Vertices in [v0, v1) with active[i] != 0 (or all, active == NULL) are
+ * decided; the others copy their label.  gains_out (optional) receives the
+ * chosen gain for movers and 0 otherwise, as two 64-bit halves.
+ * ------------------------------------------------------------------------- */
+void or_sweep(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t* w,
+              const uint32_t* labels, const uint64_t* K, const uint64_t* Sigma, const uint32_t* size,
+              uint64_t two_m, const uint32_t* bound, const uint8_t* active, int mode, int k, int uncond,
+              int nbuckets, const int64_t* deg_max, const int32_t* lanes, int vec,
+              int64_t v0, int64_t v1, uint32_t* labels_out, uint64_t* gain_lo, uint64_t* gain_hi) {
+    or_sched sched = {nbuckets, deg_max, lanes, vec};
+    (void)n;
+    int kk = k > 0 ? k : 1;
+    uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)kk);
+    uint64_t* vals = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)kk);
+    const uint32_t* bnd = (mode == MODE_REFINE) ? bound : NULL;
+    for (int64_t i = v0; i < v1; ++i) {
+        uint32_t d = labels[i];
+        labels_out[i] = d;
+        if (gain_lo) { gain_lo[i] = 0; gain_hi[i] = 0; }
+        if (active && !active[i]) continue;
+        if (mode == MODE_REFINE && size[d] != 1) continue;
+        /* candidate list */
+        int64_t deg = off[i + 1] - off[i];
+        uint32_t* cand;
+        int64_t ncand = 0;
+        if (k > 0) {
+            row_sketch(i, off, cols, w, labels, bnd, k, uncond, &sched, keys, vals);
+            cand = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)k);
+            for (int p = 0; p < k; ++p)
+                if (vals[p] > 0 && keys[p] != d) cand[ncand++] = keys[p];
+        } else {
+            cand = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(deg > 0 ? deg : 1));
+            for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+                int64_t j = cols[e];
+                if (j == i) continue;
+                if (bnd && bnd[j] != bnd[i]) continue;
+                uint32_t c = labels[j];
+                if (c == d) continue;
+                int seen = 0;
+                for (int64_t q = 0; q < ncand; ++q)
+                    if (cand[q] == c) { seen = 1; break; }
+                if (!seen) cand[ncand++] = c;
+            }
+        }
+        uint64_t Kid = link_weight(i, d, off, cols, w, labels, bnd);
+        uint32_t best = d;
+        i128 best_gain = 0;
+        uint64_t best_k = Kid;
+        int have = 0;
+        for (int64_t q = 0; q < ncand; ++q) {
+            uint32_t c = cand[q];
+            uint64_t Kic = link_weight(i, c, off, cols, w, labels, bnd);
+            if (mode == MODE_LPA) {
+                if (Kic > Kid && (Kic > best_k || (Kic == best_k && c < best))) {
+                    best = c; best_k = Kic; have = 1;
+                }
+            } else {
+                if (mode == MODE_LOUVAIN && size[d] == 1 && size[c] == 1 && c > d) continue;
+                i128 g = dq_gain(two_m, Kic, Kid, K[i], Sigma[c], Sigma[d]);
+                if (g > 0 && (g > best_gain || (g == best_gain && c < best))) {
+                    best = c; best_gain = g; have = 1;
+                }
+            }
+        }
+        free(cand);
+        if (have) {
+            labels_out[i] = best;
+            if (gain_lo) {
+                u128 g = (mode == MODE_LPA) ? (u128)(best_k - Kid) : (u128)best_gain;
+                gain_lo[i] = (uint64_t)g;
+                gain_hi[i] = (uint64_t)(g >> 64);
+            }
+        }
+    }
+    free(keys);
+    free(vals);
+}
+
+/* The MG sketch of one row on its own (for tests of the stream partition). */
+void or_row_sketch(int64_t i, const int64_t* off, const int32_t* cols, const uint32_t* w,
+                   const uint32_t* labels, const uint32_t* bound, int k, int uncond, int nbuckets,
+                   const int64_t* deg_max, const int32_t* lanes, int vec, uint32_t* keys,
+                   uint64_t* vals) {
+    or_sched sched = {nbuckets, deg_max, lanes, vec};
+    row_sketch(i, off, cols, w, labels, bound, k, uncond, &sched, keys, vals);
+}
+
+/* ---------------------------------------------------------------------------
+ * Sequential (Gauss-Seidel) local-moving phase, one vertex at a time in id
+ * order, each move updating Sigma at once (the paper's per-thread loop with
+ * a single thread).  Sketches are one stream per row in CSR order.
+ * Louvain: repeats sweeps until the sweep's summed delta-modularity is at
+ * most tol (compared as gain_sum <= tol * 2m^2), or max_sweeps.
+ * LPA: repeats until at most tol * n vertices changed label, or max_sweeps.
+ * labels is updated in place; returns the number of sweeps.
+ * ------------------------------------------------------------------------- */
+int or_local_move_seq(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t* w,
+                      uint32_t* labels, int mode, int k, int uncond, double tol, int max_sweeps) {
+    uint64_t* K = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint64_t* Sig = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t* size = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    or_degrees(n, off, w, K);
+    or_community_totals(n, labels, K, Sig, size);
+    uint64_t two_m = 0;
+    for (int64_t i = 0; i < n; ++i) two_m += K[i];
+    int kk = k > 0 ? k : 1;
+    uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)kk);
+    uint64_t* vals = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)kk);
+    int64_t one_stream_deg = INT64_MAX;
+    int32_t one_lane = 1;
+    or_sched sched = {1, &one_stream_deg, &one_lane, 1};
+    int sweeps = 0;
+    for (; sweeps < max_sweeps;) {
+        ++sweeps;
+        u128 gain_sum = 0;
+        int64_t moved = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t d = labels[i];
+            int64_t deg = off[i + 1] - off[i];
+            uint32_t* cand = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(deg > kk ? deg : kk));
+            int64_t ncand = 0;
+            if (k > 0) {
+                row_sketch(i, off, cols, w, labels, NULL, k, uncond, &sched, keys, vals);
+                for (int p = 0; p < k; ++p)
+                    if (vals[p] > 0 && keys[p] != d) cand[ncand++] = keys[p];
+            } else {
+                for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+                    if (cols[e] == i) continue;
+                    uint32_t c = labels[cols[e]];
+                    if (c == d) continue;
+                    int seen = 0;
+                    for (int64_t q = 0; q < ncand; ++q)
+                        if (cand[q] == c) { seen = 1; break; }
+                    if (!seen) cand[ncand++] = c;
+                }
+            }
+            uint64_t Kid = link_weight(i, d, off, cols, w, labels, NULL);
+            uint32_t best = d;
+            i128 best_gain = 0;
+            uint64_t best_k = Kid;
+            int have = 0;
+            for (int64_t q = 0; q < ncand; ++q) {
+                uint32_t c = cand[q];
+                uint64_t Kic = link_weight(i, c, off, cols, w, labels, NULL);
+                if (mode == MODE_LPA) {
+                    if (Kic > Kid && (Kic > best_k || (Kic == best_k && c < best))) {
+                        best = c; best_k = Kic; have = 1;
+                    }
+                } else {
+                    i128 g = dq_gain(two_m, Kic, Kid, K[i], Sig[c], Sig[d]);
+                    if (g > 0 && (g > best_gain || (g == best_gain && c < best))) {
+                        best = c; best_gain = g; have = 1;
+                    }
+                }
+            }
+            free(cand);
+            if (have) {
+                Sig[d] -= K[i]; size[d] -= 1;
+                Sig[best] += K[i]; size[best] += 1;
+                labels[i] = best;
+                moved += 1;
+                gain_sum += (u128)best_gain;
+            }
+        }
+        if (mode == MODE_LPA) {
+            if ((double)moved <= tol * (double)n) break;
+        } else {
+            double dq = (double)gain_sum / ((double)two_m * (double)two_m / 2.0);
+            if (dq <= tol) break;
+        }
+    }
+    free(K); free(Sig); free(size); free(keys); free(vals);
+    return sweeps;
+}
