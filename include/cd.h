@@ -1,0 +1,202 @@
+/*
+ * cd.h - C ABI of the GB300 MG-sketch community-detection library.
+ *
+ * The library implements the local-moving sweep of Louvain, Leiden and LPA
+ * with the weighted Misra-Gries (MG) sketch of arXiv 2411.02268 (Section 4,
+ * Algorithm 1 in Appendix A.1) in hand-written sm_103a CUDA kernels, with an
+ * exact per-vertex hashtable variant beside it (the paper's "Default",
+ * Section 4, Fig. 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Graph: undirected, both directions stored, CSR (Section 3: G = (V, E, w),
+ *   w_ij = w_ji > 0).  offsets int64[n+1], cols int32[nnz], weights
+ *   uint32[nnz].  Rows need not be sorted, but every result that depends on
+ *   the order of a row (the MG sketch) follows the stored order.  A
+ *   self-loop entry (i, i) counts in K_i and is skipped by the sweep
+ *   (Algorithm 1, "exclude self").  n must be below 2^31 - 1 and every
+ *   weight at least 1.
+ * Memory: `memory` = CD_MEM_DEVICE means every array argument of the call
+ *   (graph, labels, masks, outputs) is a device pointer of the current
+ *   device; CD_MEM_HOST means they are host pointers and the library copies
+ *   them in and out inside the call.  Device cols and weights must be 16-byte
+ *   aligned (cudaMalloc memory is).  The caller owns every buffer it passes;
+ *   the library only reads inputs and writes outputs.
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Kernels are enqueued on it.  Calls that return host scalars (counts,
+ *   modularity) synchronise the stream before returning.
+ * Scratch: device scratch is allocated with cudaMallocAsync on the stream and
+ *   freed before the call returns; its peak size is in cd_last_stats().
+ * Errors: every entry point returns CD_OK (0) or a negative code; it never
+ *   aborts or traps.  cd_strerror() names the code.  After CD_ECUDA the
+ *   CUDA error string is in cd_last_stats()->cuda_error.
+ * Threads: entry points may be called from several host threads; the
+ *   statistics of the last call are kept per thread.
+ */
+#ifndef CD_H
+#define CD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CD_OK 0
+#define CD_EINVAL (-1)    /* bad graph, labels or parameters */
+#define CD_ENOMEM (-2)    /* device or host allocation failed */
+#define CD_ECUDA (-3)     /* a CUDA call or kernel launch failed */
+#define CD_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define CD_EOVERFLOW (-5) /* a weight sum does not fit the integer type */
+#define CD_ENOTIMPL (-6)  /* entry point or option not available */
+
+/* sweep modes */
+#define CD_MODE_LOUVAIN 0 /* delta-modularity, Eq. 2 (Section 3.3, 4.1) */
+#define CD_MODE_LPA 1     /* maximum linking weight (Section 3.5, 4.3) */
+#define CD_MODE_REFINE 2  /* Leiden refinement (Section 3.4, 4.2) */
+
+/* memory kinds */
+#define CD_MEM_DEVICE 0
+#define CD_MEM_HOST 1
+
+typedef struct cd_csr {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* offsets; /* n+1 entries, offsets[0] = 0, nondecreasing */
+    const int32_t* cols;    /* nnz entries in [0, n) */
+    const uint32_t* weights;/* nnz entries >= 1 */
+    int32_t memory;         /* CD_MEM_DEVICE or CD_MEM_HOST */
+} cd_csr;
+
+/*
+ * Stream schedule of the MG sketch (no counterpart in the paper, which
+ * streams every row on one thread; this fixes how a row is split so that the
+ * result is deterministic).  A row of length deg falls in the first bucket b
+ * with deg <= deg_max[b] (the last bucket takes the rest) and is split into
+ * lanes[b] streams: entry e of the row (e = global CSR index) belongs to
+ * stream (e / vec) mod lanes[b], each stream feeds Algorithm 1 in increasing
+ * e, and the partial sketches are combined by the tree
+ * S[s] <- merge(S[s], S[s + o]) for o = lanes/2, ..., 1 and all s < o, where
+ * merge(A, B) feeds every slot of B with a positive value, in slot order, to
+ * A as one Algorithm 1 update.  lanes[b] is a power of two in [1, 256];
+ * deg_max ascending; vec must be 4.
+ */
+#define CD_MAX_BUCKETS 16
+typedef struct cd_schedule {
+    int32_t nbuckets;
+    int32_t vec;
+    int64_t deg_max[CD_MAX_BUCKETS];
+    int32_t lanes[CD_MAX_BUCKETS];
+} cd_schedule;
+
+typedef struct cd_params {
+    int32_t k;            /* MG slots: 1, 2, 4, 8 or 16; 0 = exact hashtable */
+    int32_t subtract;     /* 0 = conditional (Algorithm 1), 1 = unconditional (Section 4.1) */
+    double tolerance;     /* Louvain: stop a pass when the sweep's summed delta-Q <= tolerance;
+                             LPA: stop when at most tolerance * n labels changed (Section 3.5) */
+    double tolerance_drop;/* Louvain: tolerance divided by this after each pass (>= 1) */
+    double aggregation_tolerance; /* stop when |V'| > aggregation_tolerance * |V| */
+    int32_t max_sweeps;   /* sweeps per pass (LPA: iterations) */
+    int32_t max_passes;   /* Louvain/Leiden passes */
+    const cd_schedule* sched; /* NULL = cd_default_schedule(k) */
+    void* stream;         /* cudaStream_t */
+    int32_t timing;       /* nonzero: time the sweep kernel with CUDA events on `stream`
+                             (adds one event pair per sweep; see cd_stats) */
+} cd_params;
+
+typedef struct cd_stats {
+    int64_t sweeps;          /* sweeps run by the last call (all passes) */
+    int64_t passes;          /* passes (levels) of the last Louvain/Leiden call */
+    int64_t moved;           /* vertices that changed label in the last sweep */
+    uint64_t gain_lo, gain_hi;  /* last sweep: sum of scaled gains of movers (128-bit) */
+    int64_t communities;     /* communities in the result */
+    int64_t scratch_bytes;   /* peak device scratch of the last call */
+    double sweep_kernel_ms;  /* total sweep-kernel time (timing != 0), CUDA events */
+    int64_t sweep_kernel_launches;
+    double modularity;       /* last modularity computed */
+    char cuda_error[128];
+} cd_stats;
+
+/* Modularity parts (Eq. 1): Q = (two_m * sigma_in - sum_Sigma2) / two_m^2
+ * where sigma_in = sum_c sigma_c and sum_Sigma2 = sum_c Sigma_c^2. */
+typedef struct cd_modularity_parts {
+    uint64_t sigma_in;
+    uint64_t sum_sq_lo, sum_sq_hi;
+    uint64_t two_m;
+} cd_modularity_parts;
+
+/* Name of a status code (static string). */
+const char* cd_strerror(int code);
+
+/* Statistics of the calling thread's last entry-point call. */
+int cd_last_stats(cd_stats* out);
+
+/* The schedule used when cd_params.sched is NULL, for sketch size k. */
+int cd_default_schedule(int k, cd_schedule* out);
+
+/*
+ * One synchronous local-moving sweep (Section 4.1, Fig. 2; Section 4.3 for
+ * LPA; Section 4.2 for refinement).  Every vertex decides from the state at
+ * the start of the sweep:
+ *   K_i, Sigma_c and community sizes are computed from labels_in;
+ *   candidates: the slots of the row's MG sketch (k > 0) with a positive
+ *   value, or every neighbouring community (k = 0), except the current
+ *   community d = labels_in[i];
+ *   K_{i->c} for every candidate and for d from a second scan of the row
+ *   (self-loops skipped; in refine mode only neighbours j with
+ *   bound[j] == bound[i]);
+ *   Louvain/refine: gain(c) = 2m (K_{i->c} - K_{i->d}) - K_i (K_i + Sigma_c - Sigma_d)
+ *   (Eq. 2 times 2m^2, exact 128-bit integers); a vertex whose community is
+ *   a singleton may not join another singleton community with a larger id;
+ *   the largest gain wins, ties to the smaller id; the vertex moves iff the
+ *   gain is positive.  Refine additionally moves only vertices whose
+ *   community is a singleton.
+ *   LPA: the largest K_{i->c} wins, ties to the smaller id; the vertex moves
+ *   iff it exceeds K_{i->d}.
+ * labels_in: n labels in [0, n).  active: NULL or n bytes (0 = keep label).
+ * bound: n labels (refine mode only, else NULL).  labels_out: n labels
+ * (must not alias labels_in).  moved_out, gain_out (host, may be NULL):
+ * number of movers and the 128-bit sum of their gains (LPA: of
+ * K_{i->c} - K_{i->d}) as gain_out[0] (low) and gain_out[1] (high).
+ * Returns CD_EOVERFLOW if 2m does not fit 63 bits.
+ */
+int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labels_in,
+             const uint8_t* active, const uint32_t* bound, uint32_t* labels_out,
+             int64_t* moved_out, uint64_t* gain_out);
+
+/* Modularity of `labels` (Eq. 1, Section 3.2) from exact integer parts.
+ * labels: n labels in [0, n).  q_out, parts (host, either may be NULL). */
+int cd_modularity(const cd_csr* g, const uint32_t* labels, void* stream, double* q_out,
+                  cd_modularity_parts* parts);
+
+/* Louvain (Section 3.3, 4.1): passes of synchronous local-moving sweeps
+ * followed by aggregation into the super-vertex graph (renumbering by
+ * prefix scan, super-edges by sort and segmented sum), until a pass moves
+ * nobody, |V'| > aggregation_tolerance |V|, or max_passes.  labels_out: n
+ * dense community ids (ascending order of first appearance by id);
+ * q_out (host, may be NULL): modularity of the result on the input graph. */
+int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out);
+
+/* LPA (Section 3.5, 4.3): synchronous iterations from singleton labels until
+ * at most tolerance * n labels change or max_sweeps.  Same outputs. */
+int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out);
+
+/* Leiden (Section 3.4, 4.2).  Same outputs. */
+int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out);
+
+/* Aggregation step on its own (Section 3.3): labels (n, any ids < n) are
+ * renumbered densely in ascending id order (dense_out, n entries) and the
+ * super-vertex graph is written to offsets_out (n+1 capacity), cols_out and
+ * weights_out (nnz capacity each); *n_out and *nnz_out (host) receive its
+ * size.  Rows are sorted by column; the self-loop of c holds the summed
+ * weight of both directions of c's internal edges.  Device memory only. */
+int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t* dense_out,
+                 int64_t* offsets_out, int32_t* cols_out, uint32_t* weights_out,
+                 int64_t* n_out, int64_t* nnz_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CD_H */

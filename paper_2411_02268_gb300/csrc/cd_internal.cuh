@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cd.h"
+
+namespace cdk {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // key of a never-used sketch slot
+constexpr int kBlock = 256;               // threads per block of the sweep kernels
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// Device-side scalars of one call.
+struct Globals {
+    unsigned long long two_m;    // sum of K_i
+    unsigned long long max_k;    // max K_i
+    unsigned long long moved;    // movers in the last sweep
+    unsigned long long gain_lo;  // 128-bit sum of movers' gains
+    unsigned long long gain_hi;
+    unsigned long long sigma_in; // modularity: sum_c sigma_c
+    unsigned long long sq_lo;    // modularity: sum_c Sigma_c^2
+    unsigned long long sq_hi;
+    unsigned long long count;    // generic counter (renumbering)
+    unsigned int err;            // nonzero: a device-side check failed
+    unsigned int pad;
+};
+
+// Buckets of vertices by row length; bucket b holds verts[vbegin[b], vbegin[b+1])
+// and is processed by grid blocks [bbegin[b], bbegin[b+1]).
+struct BucketTable {
+    int nb;
+    int lanes[CD_MAX_BUCKETS];
+    int64_t deg_max[CD_MAX_BUCKETS];
+    int64_t vbegin[CD_MAX_BUCKETS + 1];
+    int64_t bbegin[CD_MAX_BUCKETS + 1];
+};
+
+struct SweepArgs {
+    const int64_t* off;
+    const int32_t* cols;
+    const uint32_t* w;
+    const uint32_t* labels;   // sweep-start labels
+    const uint64_t* K;
+    const uint64_t* Sigma;
+    const uint32_t* size;
+    const uint8_t* active;    // may be null
+    const uint32_t* bound;    // refine mode only
+    uint32_t* labels_out;
+    uint32_t* movers;         // optional list of movers (driver), capacity n
+    Globals* glob;
+    const uint32_t* verts;    // bucket-ordered vertex ids
+    int64_t n;
+    int64_t nnz;
+    int mode;
+    int uncond;
+    BucketTable bt;
+};
+
+// Host-side launchers (sweep.cu).
+cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,
+                           uint64_t* K, Globals* glob, cudaStream_t s);
+cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,
+                          uint32_t* size, Globals* glob, cudaStream_t s);
+// Bucketing: tile_counts / tile_offsets need nb * bucket_tiles(n) entries;
+// bucket_starts (nb + 1 int64) receives the first index of every bucket in
+// verts and the total.  Rows of length 0 are not listed; their label is
+// copied from labels_in to labels_out when labels_out is not null.
+int64_t bucket_tiles(int64_t n);
+cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt,
+                          uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
+                          uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
+                          Globals* glob, cudaStream_t s);
+cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
+cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in,
+                          const uint32_t* labels_out, const uint64_t* K, int64_t n,
+                          uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s);
+
+// sweep_exact.cu
+size_t exact_group_smem(int G, uint32_t T);
+cudaError_t launch_exact_group(const SweepArgs& a, int bucket, int G, uint32_t T, cudaStream_t s);
+cudaError_t launch_exact_block(const SweepArgs& a, int bucket, uint32_t T_smem, uint32_t* gkeys,
+                               unsigned long long* gvals, const int64_t* table_off, cudaStream_t s);
+cudaError_t launch_exact_table_sizes(const SweepArgs& a, int bucket, int64_t* sizes, cudaStream_t s);
+
+// modularity.cu: Sigma_scratch and sizes_scratch hold n entries; glob->two_m,
+// sigma_in, sq_lo and sq_hi must be zero on entry.
+cudaError_t launch_modularity(const int64_t* off, const int32_t* cols, const uint32_t* w,
+                              const uint32_t* labels, int64_t n, int64_t nnz, const uint64_t* K,
+                              uint64_t* Sigma_scratch, uint32_t* sizes_scratch, Globals* glob,
+                              cudaStream_t s);
+
+// Device-side error flags (Globals::err bits).
+constexpr unsigned kErrBadOffsets = 1u;
+constexpr unsigned kErrBadCol = 2u;
+constexpr unsigned kErrZeroWeight = 4u;
+constexpr unsigned kErrBadLabel = 8u;
+
+}  // namespace cdk

@@ -1,0 +1,86 @@
+// Modularity (Eq. 1, Section 3.2) in exact integers:
+//   Q = (2m * sum_c sigma_c - sum_c Sigma_c^2) / (2m)^2,
+// sum_c sigma_c = sum of w over CSR entries (i, j) with C_i = C_j, and
+// Sigma_c = sum of K_i over the members of c.
+#include "cd_internal.cuh"
+
+namespace cdk {
+
+constexpr int kQChunk = 64;
+
+// sum_c sigma_c: each thread scans a 64-entry chunk of the CSR and walks the
+// rows it covers.
+__global__ void k_sigma_in(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                           const uint32_t* __restrict__ w, const uint32_t* __restrict__ labels, int64_t n,
+                           int64_t nnz, Globals* glob) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t e0 = t * kQChunk;
+    unsigned long long sum = 0;
+    if (e0 < nnz) {
+        int64_t e1 = e0 + kQChunk < nnz ? e0 + kQChunk : nnz;
+        int64_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (off[mid] <= e0) lo = mid; else hi = mid;
+        }
+        int64_t r = lo, rend = off[r + 1];
+        uint32_t cr = labels[r];
+        for (int64_t e = e0; e < e1; ++e) {
+            while (e >= rend && r + 1 < n) {
+                ++r;
+                rend = off[r + 1];
+                cr = labels[r];
+            }
+            if (e >= rend) { atomicOr(&glob->err, kErrBadOffsets); break; }
+            uint32_t j = (uint32_t)cols[e];
+            if (j >= (uint32_t)n) { atomicOr(&glob->err, kErrBadCol); continue; }
+            if (__ldg(labels + j) == cr) sum += w[e];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&glob->sigma_in, sum);
+}
+
+// sum_c Sigma_c^2 as a 128-bit integer (two 64-bit halves with carry).
+__global__ void k_sum_sq(const unsigned long long* __restrict__ Sigma, int64_t n, Globals* glob) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    u128 sq = 0;
+    if (c < n) {
+        unsigned long long s = Sigma[c];
+        sq = (u128)s * (u128)s;
+    }
+    unsigned long long lo = (unsigned long long)sq, hi = (unsigned long long)(sq >> 64);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    if ((threadIdx.x & 31) == 0 && (lo | hi)) {
+        unsigned long long old = atomicAdd(&glob->sq_lo, lo);
+        unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+        if (hi + carry) atomicAdd(&glob->sq_hi, hi + carry);
+    }
+}
+
+// Sigma_scratch: n entries; sizes_scratch: n entries.  glob->two_m, sigma_in,
+// sq_lo and sq_hi must be zero on entry.
+cudaError_t launch_modularity(const int64_t* off, const int32_t* cols, const uint32_t* w,
+                              const uint32_t* labels, int64_t n, int64_t nnz, const uint64_t* K,
+                              uint64_t* Sigma_scratch, uint32_t* sizes_scratch, Globals* glob,
+                              cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = launch_totals(labels, K, n, Sigma_scratch, sizes_scratch, glob, s);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) {
+        int64_t threads = (nnz + kQChunk - 1) / kQChunk;
+        k_sigma_in<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(off, cols, w, labels, n, nnz, glob);
+    }
+    k_sum_sq<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const unsigned long long*)Sigma_scratch, n, glob);
+    return cudaGetLastError();
+}
+
+}  // namespace cdk

@@ -1,0 +1,275 @@
+// Per-pass kernels around the local-moving sweep: weighted degrees and
+// community totals (Section 3), degree bucketing, the dispatch of the MG
+// sweep by sketch size, and the commit of moves into Sigma and sizes.
+#include <cstdio>
+
+#include "cd_internal.cuh"
+
+namespace cdk {
+
+// ---------------------------------------------------------------------------
+// K_i = sum of w over row i (Section 3).  Each thread sums a 64-entry chunk of
+// the weight array and adds per-row partial sums with atomics, so hub rows
+// are split across threads and every thread does the same work.
+// ---------------------------------------------------------------------------
+constexpr int kDegChunk = 64;
+
+__global__ void k_degrees(const int64_t* __restrict__ off, const uint32_t* __restrict__ w,
+                          int64_t n, int64_t nnz, unsigned long long* __restrict__ K, Globals* glob) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t e0 = t * kDegChunk;
+    if (e0 >= nnz) return;
+    int64_t e1 = e0 + kDegChunk < nnz ? e0 + kDegChunk : nnz;
+    int64_t lo = 0, hi = n;  // off[lo] <= e0 < off[hi] (or hi == n)
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= e0) lo = mid; else hi = mid;
+    }
+    int64_t r = lo, rend = off[r + 1];
+    unsigned long long sum = 0;
+    bool zero = false;
+    for (int64_t e = e0; e < e1; ++e) {
+        while (e >= rend && r + 1 < n) {
+            if (sum) atomicAdd(&K[r], sum);
+            sum = 0;
+            ++r;
+            rend = off[r + 1];
+        }
+        if (e >= rend) {  // offsets do not cover the entries
+            atomicOr(&glob->err, kErrBadOffsets);
+            return;
+        }
+        uint32_t x = __ldg(w + e);
+        zero |= x == 0;
+        sum += x;
+    }
+    if (sum) atomicAdd(&K[r], sum);
+    if (zero) atomicOr(&glob->err, kErrZeroWeight);
+}
+
+cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,
+                           uint64_t* K, Globals* glob, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(K, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
+    if (e != cudaSuccess || nnz == 0) return e;
+    int64_t threads = (nnz + kDegChunk - 1) / kDegChunk;
+    int64_t blocks = (threads + 255) / 256;
+    k_degrees<<<(unsigned)blocks, 256, 0, s>>>(off, w, n, nnz, (unsigned long long*)K, glob);
+    return cudaGetLastError();
+}
+
+// Sigma_c and |c| from labels; 2m and max K_i into the globals.
+__global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned long long* __restrict__ K,
+                         int64_t n, unsigned long long* __restrict__ Sigma, uint32_t* __restrict__ size,
+                         Globals* glob) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long k = 0;
+    if (i < n) {
+        k = K[i];
+        uint32_t c = labels[i];
+        if ((int64_t)c < n) {
+            if (k) atomicAdd(&Sigma[c], k);
+            atomicAdd(&size[c], 1u);
+        } else {
+            atomicOr(&glob->err, kErrBadLabel);
+        }
+    }
+    unsigned long long s = k, m = k;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        unsigned long long mo = __shfl_down_sync(0xffffffffu, m, o);
+        m = mo > m ? mo : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (s) atomicAdd(&glob->two_m, s);
+        if (m) atomicMax(&glob->max_k, m);
+    }
+}
+
+cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,
+                          uint32_t* size, Globals* glob, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(Sigma, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), s);
+    if (e != cudaSuccess || n == 0) return e;
+    k_totals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(labels, (const unsigned long long*)K, n,
+                                                          (unsigned long long*)Sigma, size, glob);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Degree bucketing.  Rows of length 0 never move (their label is copied);
+// the others are listed per bucket in ascending vertex id (stable), so that
+// neighbouring groups of a warp get rows of similar length.
+// ---------------------------------------------------------------------------
+constexpr int kBucketTile = 2048;  // vertices per block, 8 rounds of 256
+
+__device__ __forceinline__ int bucket_of(int64_t deg, const BucketTable& bt) {
+    if (deg == 0) return -1;
+#pragma unroll
+    for (int b = 0; b < CD_MAX_BUCKETS; ++b)
+        if (b < bt.nb && deg <= bt.deg_max[b]) return b;
+    return bt.nb - 1;
+}
+
+int64_t bucket_tiles(int64_t n) { return (n + kBucketTile - 1) / kBucketTile; }
+
+__global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt,
+                               uint32_t* __restrict__ tile_counts, int64_t ntiles, Globals* glob) {
+    __shared__ uint32_t cnt[CD_MAX_BUCKETS];
+    if (threadIdx.x < CD_MAX_BUCKETS) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kBucketTile;
+    for (int r = 0; r < kBucketTile / 256; ++r) {
+        int64_t v = base + r * 256 + threadIdx.x;
+        if (v < n) {
+            int64_t o0 = off[v], o1 = off[v + 1];
+            bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
+            if (bad) atomicOr(&glob->err, kErrBadOffsets);
+            int b = bad ? -1 : bucket_of(o1 - o0, bt);
+            if (b >= 0) atomicAdd(&cnt[b], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < bt.nb) tile_counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Single-block exclusive scan of a moderate array (tile counts); also writes
+// the total to *total.
+__global__ void k_scan_small(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t m,
+                             unsigned long long* total) {
+    __shared__ unsigned long long part[1024];
+    int64_t per = (m + blockDim.x - 1) / blockDim.x;
+    int64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
+    unsigned long long s = 0;
+    for (int64_t x = a; x < b; ++x) s += in[x];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        unsigned long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - s;
+    for (int64_t x = a; x < b; ++x) {
+        uint32_t v = in[x];
+        out[x] = (uint32_t)run;
+        run += v;
+    }
+    if (threadIdx.x == blockDim.x - 1 && total) *total = part[threadIdx.x];
+}
+
+__global__ void k_bucket_scatter(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt,
+                                 const uint32_t* __restrict__ tile_offsets, int64_t ntiles,
+                                 uint32_t* __restrict__ verts, const uint32_t* __restrict__ labels_in,
+                                 uint32_t* __restrict__ labels_out) {
+    __shared__ uint32_t wc[8][CD_MAX_BUCKETS];
+    __shared__ uint32_t run[CD_MAX_BUCKETS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < CD_MAX_BUCKETS) run[threadIdx.x] = 0;
+    int64_t base = (int64_t)blockIdx.x * kBucketTile;
+    for (int r = 0; r < kBucketTile / 256; ++r) {
+        if (threadIdx.x < 8 * CD_MAX_BUCKETS) wc[threadIdx.x / CD_MAX_BUCKETS][threadIdx.x % CD_MAX_BUCKETS] = 0;
+        __syncthreads();
+        int64_t v = base + r * 256 + threadIdx.x;
+        int b = -1;
+        if (v < n) {
+            int64_t o0 = off[v], o1 = off[v + 1];
+            bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
+            b = bad ? -1 : bucket_of(o1 - o0, bt);
+            if (b < 0 && labels_out) labels_out[v] = labels_in[v];
+        }
+        unsigned peers = __match_any_sync(0xffffffffu, b);
+        unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (b >= 0 && rank == 0) wc[warp][b] = __popc(peers);
+        __syncthreads();
+        if (b >= 0) {
+            uint32_t pos = tile_offsets[(int64_t)b * ntiles + blockIdx.x] + run[b] + rank;
+            for (int q = 0; q < warp; ++q) pos += wc[q][b];
+            verts[pos] = (uint32_t)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < CD_MAX_BUCKETS) {
+            uint32_t t = 0;
+            for (int q = 0; q < 8; ++q) t += wc[q][threadIdx.x];
+            run[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_bucket_starts(const uint32_t* __restrict__ tile_offsets, int64_t ntiles, int nb,
+                                const unsigned long long* __restrict__ total, int64_t* __restrict__ starts) {
+    int b = threadIdx.x;
+    if (b < nb) starts[b] = tile_offsets[(int64_t)b * ntiles];
+    if (b == nb) starts[nb] = (int64_t)*total;
+}
+
+cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt,
+                          uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
+                          uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
+                          Globals* glob, cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (bt.nb + 1), s);
+    int64_t ntiles = bucket_tiles(n);
+    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, tile_counts, ntiles, glob);
+    k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, ntiles * bt.nb, &glob->count);
+    k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, tile_offsets, ntiles, verts,
+                                                      labels_in, labels_out);
+    k_bucket_starts<<<1, 32, 0, s>>>(tile_offsets, ntiles, bt.nb, &glob->count, bucket_starts);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_k(const SweepArgs& a, bool wide, int64_t nblocks, cudaStream_t s);
+extern template cudaError_t launch_k<1>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<2>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<4>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<8>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<16>(const SweepArgs&, bool, int64_t, cudaStream_t);
+
+cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s) {
+    if (nblocks == 0) return cudaSuccess;
+    switch (k) {
+        case 1: return launch_k<1>(a, wide, nblocks, s);
+        case 2: return launch_k<2>(a, wide, nblocks, s);
+        case 4: return launch_k<4>(a, wide, nblocks, s);
+        case 8: return launch_k<8>(a, wide, nblocks, s);
+        case 16: return launch_k<16>(a, wide, nblocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Commit: apply the moves of the last sweep to Sigma and sizes (after every
+// decision of the sweep has been taken from the sweep-start state).
+// ---------------------------------------------------------------------------
+__global__ void k_commit(const uint32_t* __restrict__ movers, const uint32_t* __restrict__ labels_in,
+                         const uint32_t* __restrict__ labels_out, const unsigned long long* __restrict__ K,
+                         unsigned long long* __restrict__ Sigma, uint32_t* __restrict__ size,
+                         const Globals* __restrict__ glob) {
+    const unsigned long long cnt = glob->moved;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t i = movers[t];
+        uint32_t d = labels_in[i], c = labels_out[i];
+        unsigned long long k = K[i];
+        atomicAdd(&Sigma[c], k);
+        atomicAdd(&Sigma[d], ~k + 1ull);
+        atomicAdd(&size[c], 1u);
+        atomicSub(&size[d], 1u);
+    }
+}
+
+cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in, const uint32_t* labels_out,
+                          const uint64_t* K, int64_t n, uint64_t* Sigma, uint32_t* size, Globals* glob,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_commit<<<(unsigned)blocks, 256, 0, s>>>(movers, labels_in, labels_out,
+                                              (const unsigned long long*)K,
+                                              (unsigned long long*)Sigma, size, glob);
+    return cudaGetLastError();
+}
+
+}  // namespace cdk

@@ -1,0 +1,6 @@
+// MG-sketch sweep kernel for sketch size k = 4.
+#include "sweep_mg.cuh"
+
+namespace cdk {
+template cudaError_t launch_k<4>(const SweepArgs&, bool, int64_t, cudaStream_t);
+}  // namespace cdk

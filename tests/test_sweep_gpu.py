@@ -1,0 +1,247 @@
+"""Parity of the CUDA sweep (through the C ABI) with the CPU oracle.
+
+One synchronous sweep from fixed labels must agree with the oracle element by
+element: every output label, the mover count and the 128-bit gain sum, for
+every sketch size, subtraction rule, mode, stream schedule (all lane counts
+1..256), on ragged graphs, hubs, self-loops, isolated vertices and the
+degenerate sizes.  All arithmetic is integer, so the bar is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_02268_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2411_02268_gb300 import _build
+    _build.build()
+    from paper_2411_02268_gb300 import cd
+    return cd, torch
+
+
+ALL_LANES = ([2, 4, 6, 8, 12, 16, 24, 32, 2**62], [1, 2, 4, 8, 16, 32, 64, 128, 256])
+WIDE = ([2**62], [256])
+MID = ([3, 40, 2**62], [1, 32, 64])
+
+
+def oracle_sched(cd, sched):
+    deg, lanes, vec = sched.as_lists()
+    return oracle.Schedule(deg, lanes, vec)
+
+
+def gpu_sweep(cd, torch, g, labels, mode, k, uncond=0, sched=None, active=None, host=False):
+    p = cd.make_params(k=k, subtract=uncond, schedule=sched)
+    if host:
+        G = cd.Graph.host(g)
+        out, moved, gain = cd.cd_sweep(G, p, mode, np.ascontiguousarray(labels, dtype=np.uint32),
+                                       active=None if active is None else np.ascontiguousarray(active, np.uint8))
+        return np.asarray(out, dtype=np.uint32), moved, gain
+    G = cd.Graph.to_device(g)
+    lab = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.uint32).view(np.int32)).cuda()
+    act = None if active is None else torch.from_numpy(np.ascontiguousarray(active, np.uint8)).cuda()
+    p.stream = torch.cuda.current_stream().cuda_stream
+    out, moved, gain = cd.cd_sweep(G, p, mode, lab, active=act)
+    return out.cpu().numpy().view(np.uint32), moved, gain
+
+
+def oracle_sweep(cd, g, labels, mode, k, uncond=0, sched=None, active=None):
+    sch = oracle_sched(cd, sched if sched is not None else cd.cd_default_schedule(k))
+    out, gains = oracle.sweep(g, labels, mode, k, bool(uncond), sch, active=active, threads=4)
+    moved = int(np.count_nonzero(out != np.asarray(labels, dtype=np.uint32)))
+    return out, moved, oracle.gain_total(gains)
+
+
+def check(cd, torch, g, labels, mode, k, uncond=0, sched=None, active=None, host=False):
+    a = gpu_sweep(cd, torch, g, labels, mode, k, uncond, sched, active, host)
+    b = oracle_sweep(cd, g, labels, mode, k, uncond, sched, active)
+    bad = np.nonzero(a[0] != b[0])[0]
+    assert len(bad) == 0, f"{len(bad)} labels differ, first at {bad[:5]}: gpu {a[0][bad[:5]]} oracle {b[0][bad[:5]]}"
+    assert a[1] == b[1]
+    assert a[2] == b[2]
+    return a
+
+
+def label_states(g, seed):
+    rng = np.random.default_rng(seed)
+    n = g.n
+    yield "singletons", np.arange(n, dtype=np.uint32)
+    yield "random", rng.integers(0, max(1, n // 7), size=n).astype(np.uint32)
+    lab, _ = oracle.sweep(g, np.arange(n, dtype=np.uint32), oracle.MODE_LOUVAIN, 0)
+    yield "after_one_sweep", lab
+
+
+GRAPHS = {
+    "sbm10k": lambda: gen.sbm_10k(1),
+    "rmat12_w16": lambda: gen.rmat(12, 16, wmax=16, seed=2),
+    "rmat11_w255_perm": lambda: gen.rmat(11, 16, wmax=255, seed=3, permute=True),
+    "ragged_loops": lambda: gen.random_graph(301, 2500, 9, seed=5, self_loops=True),
+    "grid_rewired": lambda: gen.grid(40, 50, 0.05, 16, seed=4),
+}
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k", [8, 1, 4, 16])
+def test_mg_louvain_default_schedule(env, gname, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    for _, lab in label_states(g, 1):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k)
+
+
+@pytest.mark.parametrize("gname", ["rmat12_w16", "ragged_loops", "sbm10k"])
+@pytest.mark.parametrize("sched_name", ["all_lanes", "wide", "mid"])
+@pytest.mark.parametrize("k", [2, 8, 16])
+def test_mg_all_stream_schedules(env, gname, sched_name, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    deg, lanes = {"all_lanes": ALL_LANES, "wide": WIDE, "mid": MID}[sched_name]
+    s = cd.schedule_from(deg, lanes)
+    for _, lab in label_states(g, 2):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, sched=s)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k, sched=s)
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k", [8, 2])
+def test_mg_lpa_and_unconditional(env, gname, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    s = cd.schedule_from(*ALL_LANES)
+    for _, lab in label_states(g, 3):
+        check(cd, torch, g, lab, oracle.MODE_LPA, k)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, uncond=1)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k, uncond=1, sched=s)
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+def test_exact_hashtable(env, gname):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    for _, lab in label_states(g, 4):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 0)
+        check(cd, torch, g, lab, oracle.MODE_LPA, 0)
+
+
+def test_exact_hub_rows_use_global_tables(env):
+    """Rows longer than 2048 entries take tables in device scratch."""
+    cd, torch = env
+    n = 6000
+    src = np.concatenate([np.zeros(5000, np.int64), np.arange(1, 3000)])
+    dst = np.concatenate([np.arange(1, 5001), np.arange(2, 3001)])
+    w = (np.arange(len(src)) % 13 + 1).astype(np.uint64)
+    g = gen.from_edges(n, src, dst, w)
+    assert g.degrees().max() > 4096
+    rng = np.random.default_rng(0)
+    for lab in (np.arange(n, dtype=np.uint32), rng.integers(0, 50, n).astype(np.uint32)):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 0)
+        check(cd, torch, g, lab, oracle.MODE_LPA, 0)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8)
+    stats = cd.cd_last_stats()
+    assert stats.scratch_bytes > 0
+
+
+def test_active_mask(env):
+    cd, torch = env
+    g = GRAPHS["rmat12_w16"]()
+    rng = np.random.default_rng(7)
+    act = (rng.random(g.n) < 0.4).astype(np.uint8)
+    for _, lab in label_states(g, 5):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8, active=act)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 0, active=act)
+
+
+def test_host_memory_matches_device(env):
+    cd, torch = env
+    g = GRAPHS["sbm10k"]()
+    lab = np.arange(g.n, dtype=np.uint32)
+    a = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8, host=True)
+    b = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8, host=False)
+    assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+    check(cd, torch, g, lab, oracle.MODE_LPA, 8, host=True)
+
+
+def test_wide_sketch_values(env):
+    """Weighted degrees above 2^32 switch the sketch to 64-bit values."""
+    cd, torch = env
+    big = 2**31 + 7
+    src = [0, 0, 0, 1, 2, 3, 4, 4]
+    dst = [1, 2, 3, 2, 3, 5, 5, 6]
+    w = [big, big, big, 3, big - 5, 9, big, 1]
+    g = gen.from_edges(7, src, dst, w)
+    for lab in (np.arange(7, dtype=np.uint32), np.array([0, 1, 1, 3, 4, 4, 6], np.uint32)):
+        for k in (1, 2, 8):
+            check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k)
+            check(cd, torch, g, lab, oracle.MODE_LPA, k)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, 0)
+
+
+def test_degenerate_graphs(env):
+    cd, torch = env
+    empty_edges = gen.from_edges(5, [], [], [])
+    check(cd, torch, empty_edges, np.arange(5, dtype=np.uint32), oracle.MODE_LOUVAIN, 8)
+    one = gen.from_edges(1, [0], [0], [3])       # a single self-loop
+    check(cd, torch, one, np.zeros(1, np.uint32), oracle.MODE_LOUVAIN, 8)
+    check(cd, torch, one, np.zeros(1, np.uint32), oracle.MODE_LOUVAIN, 0)
+    pair = gen.from_edges(2, [0], [1], [5])
+    check(cd, torch, pair, np.arange(2, dtype=np.uint32), oracle.MODE_LOUVAIN, 8)
+    check(cd, torch, pair, np.arange(2, dtype=np.uint32), oracle.MODE_LPA, 8)
+    # n = 0 through the host path
+    from paper_2411_02268_gb300 import cd as cdm
+    G0 = cdm.Graph(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    out, moved, gain = cdm.cd_sweep(G0, cdm.make_params(k=8), 0, np.zeros(0, np.uint32))
+    assert moved == 0 and gain == 0
+
+
+def test_two_triangles_golden(env):
+    import json, os
+    cd, torch = env
+    t = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "two_triangles.json")))
+    e = np.array(t["edges"])
+    g = gen.from_edges(t["n"], e[:, 0], e[:, 1], np.ones(len(e)))
+    for k in (0, 8):
+        out, moved, gain = gpu_sweep(cd, torch, g, np.arange(6, dtype=np.uint32), oracle.MODE_LOUVAIN, k)
+        assert out.tolist() == t["sweep1_labels"]
+        assert gain == sum(t["sweep1_gains"])
+
+
+def test_device_detects_bad_columns(env):
+    """A column out of range in a device graph is reported, not read."""
+    cd, torch = env
+    g = gen.sbm(200, 4, 0.2, 0.02, seed=3)
+    g.cols[17] = 10_000
+    G = cd.Graph.to_device(g)
+    lab = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(cd.CDError) as ei:
+        cd.cd_sweep(G, cd.make_params(k=8), 0, lab)
+    assert ei.value.code == cd.CD_EINVAL
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_modularity_parity(env, seed):
+    cd, torch = env
+    g = gen.rmat(12, 16, wmax=16, seed=seed + 10)
+    rng = np.random.default_rng(seed)
+    for lab in (np.arange(g.n, dtype=np.uint32), rng.integers(0, 30, g.n).astype(np.uint32),
+                np.zeros(g.n, np.uint32)):
+        G = cd.Graph.to_device(g)
+        q, parts = cd.cd_modularity(G, torch.from_numpy(lab.view(np.int32)).cuda())
+        sin_, sq, tm = oracle.modularity_parts(g, lab)
+        assert parts == (sin_, sq, tm)
+        assert abs(q - float(oracle.modularity_fraction(g, lab))) <= 1e-15
+        qh, parts_h = cd.cd_modularity(cd.Graph.host(g), lab)
+        assert parts_h == parts
+
+
+def test_repeatable(env):
+    cd, torch = env
+    g = GRAPHS["rmat12_w16"]()
+    lab = np.arange(g.n, dtype=np.uint32)
+    a = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8)
+    b = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8)
+    assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
