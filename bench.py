@@ -1,0 +1,335 @@
+"""Benchmark of the MG-sketch local-moving sweep on one or more GB300s.
+
+One step = one pass of the hot path over the synthetic R-MAT scale-22 graph
+(2^22 vertices, edge factor 16, (a,b,c) = (0.57, 0.19, 0.19), weights in
+[1, 16]; about 128M CSR entries): weighted degrees and degree buckets, then
+one synchronous Louvain sweep with the k = 8 weighted Misra-Gries sketch
+(sketch scan, merge tree, exact second scan, Eq. 2 decision, mover
+statistics), from singleton communities, through the C ABI (cd_sweep).
+
+Prints one JSON line (rank 0).  `value` is local-move throughput in GTEPS
+(CSR entries swept per second, all ranks), timed with CUDA events on the
+launching stream; the graph (1 GB) is larger than L2, so no flush is needed
+between steps.  `--impl reference` times the CPU oracle on the host cores on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "rmat22": dict(desc="R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
+    "rmat20": dict(desc="R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
+    "sbm10k": dict(desc="planted-partition SBM 10k vertices, 100 blocks, p_in 0.05, p_out 0.0005, w=1"),
+}
+
+
+def make_graph(name: str):
+    from paper_2411_02268_gb300 import gen
+    if name == "rmat22":
+        return gen.rmat22(1)
+    if name == "rmat20":
+        return gen.rmat(20, 16, wmax=16, seed=1)
+    if name == "sbm10k":
+        return gen.sbm_10k(1)
+    raise ValueError(name)
+
+
+def algorithmic_bytes(g, k: int) -> dict:
+    """Bytes one sweep must move at least: per CSR entry cols 4 + w 4 +
+    labels[col] 4; per vertex with edges offsets 8 + K 8 + label in 4 +
+    label out 4 + Sigma_d 8 + size 4.  Candidate Sigma_c gathers are not
+    counted (their number is data-dependent), so this is a lower bound."""
+    deg = np.diff(g.offsets)
+    n_active = int(np.count_nonzero(deg))
+    return dict(per_entry=12, per_vertex=36, entries=int(g.nnz), vertices=n_active,
+                bytes=12 * int(g.nnz) + 36 * n_active)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_02268_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("sweep") or f == "cd_internal.cuh":
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, k: int):
+    """DRAM bytes per sweep-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"sweep_mg_k{k}_{workload}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def oracle_sample(g, k: int, seconds: float, threads: int):
+    """Times the CPU oracle sweep on a growing random vertex sample until about
+    `seconds` of CPU work; returns (entries swept per second, description)."""
+    import oracle
+    from paper_2411_02268_gb300 import cd
+    sched = oracle.Schedule(*cd.cd_default_schedule(k).as_lists()) if os.path.exists(cd.SO) else \
+        oracle.Schedule([2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 32768, 2**62],
+                        [1, 1, 1, 1, 1, 2, 2, 4, 4, 8, 8, 16, 32, 128, 256], 4)
+    K = oracle.degrees(g)
+    labels = np.arange(g.n, dtype=np.uint32)
+    Sig, size = oracle.community_totals(g.n, labels, K)
+    state = (K, Sig, size, int(K.sum()))
+    deg = np.diff(g.offsets)
+    rng = np.random.default_rng(0)
+    frac = 1e-4
+    while True:
+        act = (rng.random(g.n) < frac).astype(np.uint8)
+        t0 = time.perf_counter()
+        oracle.sweep(g, labels, oracle.MODE_LOUVAIN, k, False, sched, active=act, threads=threads, state=state)
+        dt = time.perf_counter() - t0
+        entries = int(deg[act.astype(bool)].sum())
+        if dt >= seconds or frac >= 1.0:
+            return entries / dt, (f"{int(act.sum())} random vertices ({frac:.2e} of all, {entries} CSR entries) "
+                                  f"of one k={k} Louvain sweep from singletons, {threads} threads, {dt:.1f} s")
+        frac = min(1.0, frac * max(2.0, min(8.0, seconds / max(dt, 1e-3))))
+
+
+def run_reference(args, g, world):
+    """CPU oracle arm: each step is a bounded sample of the workload."""
+    threads = os.cpu_count() or 1
+    rates = []
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        r, desc = oracle_sample(g, args.k, args.ref_seconds, threads)
+        if s >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates)) / 1e9
+    line = {
+        "impl": "reference", "metric": "local-move GTEPS (Louvain, MG k=8 sweep)", "value": v, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": g.nnz / (v * 1e9) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "nnz": g.nnz, "k": args.k,
+                   "mode": "louvain", "labels": "singletons"},
+        "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=list(WORKLOADS))
+    ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, make_graph(args.workload), world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    from paper_2411_02268_gb300 import cd
+    cd.lib()
+
+    t_gen = time.perf_counter()
+    g = make_graph(args.workload)
+    t_gen = time.perf_counter() - t_gen
+    G = cd.Graph.to_device(g, f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    lab = torch.arange(g.n, dtype=torch.int32, device=f"cuda:{local}")
+    out = torch.empty_like(lab)
+    params = cd.make_params(k=args.k, stream=stream.cuda_stream, timing=True)
+
+    def step():
+        return cd.cd_sweep(G, params, cd.MODE_LOUVAIN, lab, labels_out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    kern_ms, kern_launches = 0.0, 0
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        moved = 0
+        for _ in range(args.steps):
+            _, moved, _ = step()
+            st = cd.cd_last_stats()
+            kern_ms += st.sweep_kernel_ms
+            kern_launches += st.sweep_kernel_launches
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ms_step = ms / args.steps
+    gteps = g.nnz * args.steps * world / (ms * 1e-3) / 1e9
+    scratch = cd.cd_last_stats().scratch_bytes
+
+    # end to end through the C ABI with pinned host buffers (copies inside the call)
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        Gh = cd.Graph(g.n, pin(g.offsets), pin(g.cols), pin(g.w))
+        lab_h = pin(np.arange(g.n, dtype=np.uint32))
+        out_h = pin(np.empty(g.n, dtype=np.uint32))
+        ph = cd.make_params(k=args.k, stream=stream.cuda_stream)
+        cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
+        dt = time.perf_counter() - t0
+        h2d = g.offsets.nbytes + g.cols.nbytes + g.w.nbytes + lab_h.nbytes
+        e2e = {"value": g.nnz * args.e2e_steps * world / dt / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_h.nbytes),
+               "note": "cd_sweep with host CSR/labels; host->device copy, sweep, device->host labels per step"}
+        ok = np.array_equal(out_h, out.cpu().numpy().view(np.uint32))
+        e2e["matches_device_run"] = bool(ok)
+
+    ab = algorithmic_bytes(g, args.k)
+    kern_avg_ms = kern_ms / max(kern_launches, 1)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = ab["bytes"] / (kern_avg_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload, args.k)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_sweep_mg", "kernel_ms": kern_avg_ms,
+                "algorithmic_bytes": ab["bytes"], "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, desc = oracle_sample(g, args.k, args.cpu_seconds, threads)
+        cpu = {"value": r / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "local-move GTEPS (Louvain, MG k=8 sweep)", "value": gteps, "unit": "GTEPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "nnz": g.nnz, "k": args.k,
+                       "mode": "louvain", "labels": "singletons", "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas{world}", "scratch_bytes": scratch, "moved": moved,
+                       "gen_seconds": round(t_gen, 2)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 7 * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
