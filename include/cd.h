@@ -103,6 +103,10 @@ typedef struct cd_params {
     void* stream;         /* cudaStream_t */
     int32_t timing;       /* nonzero: time the sweep kernel with CUDA events on `stream`
                              (adds one event pair per sweep; see cd_stats) */
+    int32_t colors;       /* drivers: each sweep is `colors` sub-sweeps, sub-sweep p deciding
+                             the vertices i with lowbias32(i) mod colors = p from the state
+                             left by the previous sub-sweeps (1 = fully synchronous sweeps,
+                             0 = default 8, at most 16); cd_sweep ignores it */
 } cd_params;
 
 typedef struct cd_stats {

@@ -355,3 +355,86 @@ def brute_force_best(g):
         if best is None or q > best:
             best, arg = q, lab
     return best, arg
+
+
+# ---- synchronous whole algorithms (the schedule the CUDA drivers follow) ------------------
+
+def _dq_as_double(gain: int, two_m: int) -> float:
+    """Summed scaled gain -> delta-Q in double, rounded the way the library
+    does it: high and low 64-bit halves converted separately."""
+    hi, lo = gain >> 64, gain & (2**64 - 1)
+    return (float(hi) * 18446744073709551616.0 + float(lo)) / (float(two_m) * float(two_m) / 2.0)
+
+
+def color_classes(n: int, colors: int) -> np.ndarray:
+    """Colour class of every vertex: the 32-bit integer hash lowbias32
+    (C. Wellons) of the vertex id, modulo the number of classes."""
+    if colors <= 1:
+        return np.zeros(n, dtype=np.uint32)
+    x = np.arange(n, dtype=np.uint32)
+    x ^= x >> np.uint32(16)
+    x *= np.uint32(0x7FEB352D)
+    x ^= x >> np.uint32(15)
+    x *= np.uint32(0x846CA68B)
+    x ^= x >> np.uint32(16)
+    return x % np.uint32(colors)
+
+
+def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, colors=8):
+    """Local-moving phase from singletons, each sweep made of `colors`
+    sub-sweeps: sub-sweep p decides the vertices of colour class p, all at
+    once, from the state left by the previous sub-sweeps (colors=1: fully
+    synchronous sweeps).  Stops when nobody moves in a sweep, the sweep's
+    summed delta-Q is <= tol (Louvain) or at most tol * n labels changed
+    (LPA), or after max_sweeps.  Returns (labels, sweeps)."""
+    n = g.n
+    labels = np.arange(n, dtype=np.uint32)
+    K = degrees(g)
+    two_m = int(K.sum(dtype=np.uint64))
+    col = color_classes(n, colors)
+    masks = [(col == p).astype(np.uint8) for p in range(max(colors, 1))]
+    sweeps = 0
+    while sweeps < max_sweeps:
+        moved, gsum = 0, 0
+        for act in masks:
+            Sig, size = community_totals(n, labels, K)
+            out, gains = sweep(g, labels, mode, k, uncond, sched, active=act if colors > 1 else None,
+                               threads=threads, state=(K, Sig, size, two_m))
+            moved += int(np.count_nonzero(out != labels))
+            gsum += gain_total(gains)
+            labels = out
+        sweeps += 1
+        if moved == 0:
+            break
+        if mode == MODE_LPA:
+            if float(moved) <= tol * float(n):
+                break
+        elif _dq_as_double(gsum, two_m) <= tol:
+            break
+    return labels, sweeps
+
+
+def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
+                 agg_tol=0.8, sched=None, threads=1, colors=8):
+    """Louvain with colour-class sub-sweeps: the exact schedule of cd_louvain."""
+    sched = sched or Schedule.single_stream()
+    top = np.arange(g.n, dtype=np.uint32)
+    cur = g
+    for p in range(max_passes):
+        if cur.n == 0:
+            break
+        lab, _ = local_move_sync(cur, MODE_LOUVAIN, k, uncond, tol, max_sweeps, sched, threads, colors)
+        dense, nc = renumber(lab)
+        top = dense[top]
+        if nc == cur.n or nc > agg_tol * cur.n or p + 1 >= max_passes:
+            break
+        cur, _ = aggregate(cur, dense)
+        tol /= tol_drop
+    return top
+
+
+def lpa_sync(g, k=8, uncond=False, tol=0.05, max_sweeps=20, sched=None, threads=1, colors=8):
+    """LPA with colour-class sub-sweeps: the exact schedule of cd_lpa."""
+    sched = sched or Schedule.single_stream()
+    lab, _ = local_move_sync(g, MODE_LPA, k, uncond, tol, max_sweeps, sched, threads, colors)
+    return renumber(lab)[0]

@@ -2,6 +2,7 @@
 // scratch, the launch sequence of one sweep, modularity, and host-memory
 // staging.  Every entry point returns a status code and never aborts.
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -72,13 +73,12 @@ int check_csr(const cd_csr* g) {
     if (g->memory == CD_MEM_DEVICE && g->nnz > 0 && (!aligned16(g->cols) || !aligned16(g->weights)))
         return CD_EINVAL;
     if (g->memory == CD_MEM_HOST) {
-        // full structural check on the host
+        // offsets are checked here; columns and weights are checked by the
+        // kernels that read them (device-side error flags)
         const int64_t* off = g->offsets;
         if (off[0] != 0 || off[g->n] != g->nnz) return CD_EINVAL;
         for (int64_t i = 0; i < g->n; ++i)
             if (off[i + 1] < off[i]) return CD_EINVAL;
-        for (int64_t e = 0; e < g->nnz; ++e)
-            if (g->cols[e] < 0 || g->cols[e] >= g->n || g->weights[e] == 0) return CD_EINVAL;
     }
     return CD_OK;
 }
@@ -153,14 +153,35 @@ struct Level {
     uint32_t* size = nullptr;
     uint32_t* verts = nullptr;
     uint32_t* movers = nullptr;
-    BucketTable bt;
+    BucketTable bt;     // bucket layout; ranges of colour class 0
+    int colors = 1;
+    std::vector<int64_t> starts;  // (colour, bucket) range starts, colors * nb + 1
     bool wide = false;  // sketch values need 64 bits
     unsigned long long two_m = 0;
+
+    // Bucket table of colour class p (vertex ranges and grid blocks).
+    BucketTable table_for(int p) const {
+        BucketTable t = bt;
+        int64_t blk = 0;
+        for (int b = 0; b < bt.nb; ++b) {
+            t.vbegin[b] = starts[(size_t)p * bt.nb + b];
+            t.bbegin[b] = blk;
+            int64_t nv = starts[(size_t)p * bt.nb + b + 1] - t.vbegin[b];
+            int Lb = bt.lanes[b];
+            int vpb = Lb >= kBlock ? 1 : kBlock / Lb;
+            blk += (nv + vpb - 1) / vpb;
+        }
+        t.vbegin[bt.nb] = starts[(size_t)p * bt.nb + bt.nb];
+        t.bbegin[bt.nb] = blk;
+        return t;
+    }
 };
+
+constexpr int kMaxColors = 16;
 
 struct HostGlobals {
     Globals g;
-    int64_t starts[CD_MAX_BUCKETS + 1];
+    int64_t starts[kMaxColors * CD_MAX_BUCKETS + 1];
 };
 
 int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cudaStream_t s) {
@@ -169,45 +190,40 @@ int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cud
                                          cudaMemcpyDeviceToHost, s));
     CD_CUDA(cudaStreamSynchronize(s));
     unsigned err = out->g.err;
+    if (err & kErrWeightOverflow) return CD_EOVERFLOW;
     if (err) return CD_EINVAL;
     return CD_OK;
 }
 
-// K, totals from `labels`, buckets; reads back 2m, max K and bucket sizes.
+// K, totals from `labels`, buckets by (colour class, row length); reads back
+// 2m, max K and the bucket ranges.
 int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, bool exact,
-                  const cd_schedule& sched, Scratch& sc, Globals* dglob, cudaStream_t s) {
+                  const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s) {
     CD_TRY(sc.get(&L.K, L.n));
     CD_TRY(sc.get(&L.Sigma, L.n));
     CD_TRY(sc.get(&L.size, L.n));
     CD_TRY(sc.get(&L.verts, L.n));
     L.bt = exact ? exact_table() : table_from(sched);
+    L.colors = colors;
+    const int nkeys = colors * L.bt.nb;
     int64_t ntiles = bucket_tiles(L.n);
     uint32_t *tc, *to;
     int64_t* starts;
-    CD_TRY(sc.get(&tc, ntiles * L.bt.nb));
-    CD_TRY(sc.get(&to, ntiles * L.bt.nb));
-    CD_TRY(sc.get(&starts, CD_MAX_BUCKETS + 1));
+    CD_TRY(sc.get(&tc, ntiles * nkeys));
+    CD_TRY(sc.get(&to, ntiles * nkeys));
+    CD_TRY(sc.get(&starts, nkeys + 1));
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
     CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, L.K, dglob, s));
     CD_CUDA(launch_totals(labels, L.K, L.n, L.Sigma, L.size, dglob, s));
-    CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, tc, to, starts, L.verts, labels, labels_out_copy,
+    CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, colors, tc, to, starts, L.verts, labels, labels_out_copy,
                           dglob, s));
     HostGlobals hg;
-    CD_TRY(read_globals(dglob, starts, L.bt.nb, &hg, s));
+    CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
     L.two_m = hg.g.two_m;
     if (L.two_m >= (1ull << 62)) return CD_EOVERFLOW;
     L.wide = hg.g.max_k >= (1ull << 32);
-    int64_t blk = 0;
-    for (int b = 0; b < L.bt.nb; ++b) {
-        L.bt.vbegin[b] = hg.starts[b];
-        L.bt.bbegin[b] = blk;
-        int64_t nv = (b + 1 < L.bt.nb ? hg.starts[b + 1] : hg.starts[L.bt.nb]) - hg.starts[b];
-        int Lb = L.bt.lanes[b];
-        int vpb = Lb >= kBlock ? 1 : kBlock / Lb;
-        blk += (nv + vpb - 1) / vpb;
-    }
-    L.bt.vbegin[L.bt.nb] = hg.starts[L.bt.nb];
-    L.bt.bbegin[L.bt.nb] = blk;
+    L.starts.assign(hg.starts, hg.starts + nkeys + 1);
+    L.bt = L.table_for(0);
     return CD_OK;
 }
 
@@ -284,6 +300,204 @@ struct Timer {
     }
 };
 
+
+// Renumbers `labels` of level L densely (dense, n entries) and reads back the
+// number of communities.
+int renumber_level(const Level& L, const uint32_t* labels, uint32_t* dense, Scratch& sc, Globals* dglob,
+                   int64_t* nc, cudaStream_t s) {
+    uint32_t* tmp;
+    unsigned long long* tiles;
+    CD_TRY(sc.get(&tmp, L.n));
+    CD_TRY(sc.get(&tiles, scan_tiles(L.n) + 1));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(launch_renumber(labels, L.n, dense, tmp, tiles, &dglob->count, dglob, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    *nc = (int64_t)hg.g.count;
+    return CD_OK;
+}
+
+// Super-vertex graph of level L under dense labels (nc communities).  Output
+// arrays are taken from the caller (off_out n+1 >= nc+1, cols/w >= nnz) or,
+// when null, from scratch.
+int aggregate_level(const Level& L, const uint32_t* dense, int64_t nc, Scratch& sc, Globals* dglob,
+                    cudaStream_t s, int64_t* off_out, int32_t* cols_out, uint32_t* w_out, Level* next) {
+    const int64_t m = L.nnz;
+    AggScratch a;
+    CD_TRY(sc.get(&a.src, m));
+    CD_TRY(sc.get(&a.dst, m));
+    CD_TRY(sc.get(&a.w, m));
+    CD_TRY(sc.get(&a.src2, m));
+    CD_TRY(sc.get(&a.dst2, m));
+    CD_TRY(sc.get(&a.w2, m));
+    CD_TRY(sc.get(&a.heads, m));
+    CD_TRY(sc.get(&a.hist, radix_tiles(m) * 256));
+    int64_t tiles = scan_tiles(radix_tiles(m) * 256);
+    if (scan_tiles(m) > tiles) tiles = scan_tiles(m);
+    if (scan_tiles(nc + 1) > tiles) tiles = scan_tiles(nc + 1);
+    CD_TRY(sc.get(&a.tiles, tiles + 1));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(launch_expand(L.off, L.cols, L.n, m, dense, a.src, a.dst, s));
+    if (m > 0) CD_CUDA(cudaMemcpyAsync(a.w, L.w, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s));
+    CD_CUDA(radix_sort_pairs(a, m, nc, dglob, s));
+    CD_CUDA(launch_heads(a, m, s));
+    uint32_t* uidx;
+    CD_TRY(sc.get(&uidx, m));
+    CD_CUDA(launch_exclusive_scan_u32(a.heads, uidx, m, a.tiles, &dglob->count, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    const int64_t m2 = (int64_t)hg.g.count;
+    CD_TRY(sc.get(&a.wsum, m2));
+    uint32_t* rowcnt;
+    CD_TRY(sc.get(&rowcnt, nc + 1));
+    if (!off_out) {
+        CD_TRY(sc.get(&off_out, nc + 1));
+        CD_TRY(sc.get(&cols_out, m2));
+        CD_TRY(sc.get(&w_out, m2));
+    }
+    CD_CUDA(cudaMemsetAsync(a.wsum, 0, sizeof(unsigned long long) * (m2 > 0 ? m2 : 1), s));
+    CD_CUDA(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * (nc + 1), s));
+    CD_CUDA(launch_segsum(a, uidx, m, cols_out, rowcnt, s));
+    CD_CUDA(launch_narrow(a.wsum, m2, w_out, dglob, s));
+    CD_CUDA(launch_exclusive_scan_u32_to_i64(rowcnt, off_out, nc + 1, a.tiles, &dglob->count, s));
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    if (next) {
+        *next = Level();
+        next->n = nc;
+        next->nnz = m2;
+        next->off = off_out;
+        next->cols = cols_out;
+        next->w = w_out;
+    }
+    return CD_OK;
+}
+
+double gain_as_double(unsigned long long lo, unsigned long long hi) {
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// Local-moving phase on level L from singleton labels: sweeps (each followed
+// by the commit into Sigma and sizes) until nobody moves, the sweep's summed
+// delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
+// max_sweeps.  Returns the final labels in *labels (one of two scratch buffers).
+int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_schedule& sched, Scratch& sc,
+               Globals* dglob, cudaStream_t s, uint32_t** labels, int64_t* sweeps_out) {
+    uint32_t *la, *lb;
+    CD_TRY(sc.get(&la, L.n));
+    CD_TRY(sc.get(&lb, L.n));
+    CD_TRY(sc.get(&L.movers, L.n));
+    CD_CUDA(launch_iota(la, L.n, s));
+    const int colors = p->colors == 0 ? 8 : p->colors;
+    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
+    // both label buffers hold every vertex: copy the rows of length 0 as well
+    CD_CUDA(cudaMemcpyAsync(lb, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
+    std::vector<Timer> tms((size_t)colors);
+    for (auto& t : tms) CD_TRY(t.init(p->timing != 0));
+    const size_t stat_off = offsetof(Globals, moved);
+    const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
+    int64_t sw = 0;
+    for (; sw < p->max_sweeps;) {
+        CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
+        for (int c = 0; c < colors; ++c) {
+            // sub-sweep c: vertices of colour c decide from la; the others keep
+            // their label in lb, which then becomes the state of sub-sweep c+1
+            CD_CUDA(cudaMemcpyAsync(&dglob->mark, &dglob->moved, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToDevice, s));
+            Level Lc = L;
+            Lc.bt = L.table_for(c);
+            SweepArgs a = make_args(Lc, la, lb, nullptr, nullptr, dglob, mode, p->subtract);
+            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].a, s));
+            CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
+            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, s));
+            CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
+            // carry the moves of this sub-sweep into la for the next one
+            CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
+        }
+        HostGlobals hg;
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        for (auto& t : tms) {
+            if (!t.on) continue;
+            float ms = 0;
+            CD_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+            g_stats.sweep_kernel_ms += ms;
+            g_stats.sweep_kernel_launches += 1;
+        }
+        ++sw;
+        g_stats.moved = (int64_t)hg.g.moved;
+        g_stats.gain_lo = hg.g.gain_lo;
+        g_stats.gain_hi = hg.g.gain_hi;
+        if (hg.g.moved == 0) break;
+        if (mode == CD_MODE_LPA) {
+            if ((double)hg.g.moved <= tol * (double)L.n) break;
+        } else {
+            double dq = gain_as_double(hg.g.gain_lo, hg.g.gain_hi) /
+                        ((double)L.two_m * (double)L.two_m / 2.0);
+            if (dq <= tol) break;
+        }
+    }
+    *labels = la;
+    *sweeps_out = sw;
+    return CD_OK;
+}
+
+// Stages a host graph into scratch (or passes a device graph through).
+int input_level(const cd_csr* g, Scratch& sc, Level* L) {
+    L->n = g->n;
+    L->nnz = g->nnz;
+    if (g->memory == CD_MEM_HOST) {
+        int64_t* off; int32_t* cols; uint32_t* w;
+        CD_TRY(stage_in(g->offsets, g->n + 1, &off, sc));
+        CD_TRY(stage_in(g->cols, g->nnz, &cols, sc));
+        CD_TRY(stage_in(g->weights, g->nnz, &w, sc));
+        L->off = off; L->cols = cols; L->w = w;
+    } else {
+        L->off = g->offsets; L->cols = g->cols; L->w = g->weights;
+    }
+    return CD_OK;
+}
+
+int modularity_of(const Level& L, const uint32_t* labels, Scratch& sc, Globals* dglob, cudaStream_t s,
+                  double* q) {
+    uint64_t *K, *Sig;
+    uint32_t* sz;
+    CD_TRY(sc.get(&K, L.n));
+    CD_TRY(sc.get(&Sig, L.n));
+    CD_TRY(sc.get(&sz, L.n));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    if (L.n > 0) {
+        CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, K, dglob, s));
+        CD_CUDA(launch_modularity(L.off, L.cols, L.w, labels, L.n, L.nnz, K, Sig, sz, dglob, s));
+    }
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    u128 sq = ((u128)hg.g.sq_hi << 64) | (u128)hg.g.sq_lo;
+    u128 tm = hg.g.two_m;
+    *q = 0.0;
+    if (tm > 0) {
+        i128 num = (i128)(tm * (u128)hg.g.sigma_in) - (i128)sq;
+        *q = (double)((long double)num / ((long double)tm * (long double)tm));
+    }
+    g_stats.modularity = *q;
+    return CD_OK;
+}
+
+int check_driver_params(const cd_params* p) {
+    CD_TRY(check_params(p));
+    if (p->max_sweeps < 0 || p->max_passes < 0) return CD_EINVAL;
+    if (!(p->tolerance >= 0.0) || !(p->tolerance_drop >= 1.0) || !(p->aggregation_tolerance > 0.0))
+        return CD_EINVAL;
+    return CD_OK;
+}
+
+// Writes dense labels (device) to the caller's buffer (device or host).
+int emit_labels(const cd_csr* g, const uint32_t* dense, uint32_t* labels_out, cudaStream_t s) {
+    if (g->n == 0) return CD_OK;
+    cudaMemcpyKind kind = g->memory == CD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CD_CUDA(cudaMemcpyAsync(labels_out, dense, sizeof(uint32_t) * g->n, kind, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    return CD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -355,7 +569,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         if (gain_out) { gain_out[0] = 0; gain_out[1] = 0; }
         return CD_OK;
     }
-    CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, sc, dglob, s));
+    CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, 1, sc, dglob, s));
     SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract);
     Timer tm;
     CD_TRY(tm.init(p->timing != 0));
@@ -434,12 +648,110 @@ int cd_modularity(const cd_csr* g, const uint32_t* labels, void* stream, double*
     return CD_OK;
 }
 
-int cd_louvain(const cd_csr*, const cd_params*, uint32_t*, double*) { return CD_ENOTIMPL; }
-int cd_lpa(const cd_csr*, const cd_params*, uint32_t*, double*) { return CD_ENOTIMPL; }
+int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    CD_TRY(check_driver_params(p));
+    if (!labels_out) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule sched;
+    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level in;
+    CD_TRY(input_level(g, sc, &in));
+    uint32_t* top;
+    CD_TRY(sc.get(&top, in.n));
+    CD_CUDA(launch_iota(top, in.n, s));
+    Level cur = in;
+    double tol = p->tolerance;
+    int64_t ncom = in.n;
+    for (int pass = 0; pass < p->max_passes && cur.n > 0; ++pass) {
+        uint32_t* lab;
+        int64_t sw = 0;
+        CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, &lab, &sw));
+        g_stats.sweeps += sw;
+        g_stats.passes += 1;
+        uint32_t* dense;
+        CD_TRY(sc.get(&dense, cur.n));
+        int64_t nc = 0;
+        CD_TRY(renumber_level(cur, lab, dense, sc, dglob, &nc, s));
+        CD_CUDA(launch_compose(top, in.n, dense, s));
+        ncom = nc;
+        if (nc == cur.n || (double)nc > p->aggregation_tolerance * (double)cur.n) break;
+        if (pass + 1 >= p->max_passes) break;
+        Level next;
+        CD_TRY(aggregate_level(cur, dense, nc, sc, dglob, s, nullptr, nullptr, nullptr, &next));
+        cur = next;
+        tol /= p->tolerance_drop;
+    }
+    g_stats.communities = ncom;
+    double q = 0.0;
+    CD_TRY(modularity_of(in, top, sc, dglob, s, &q));
+    CD_TRY(emit_labels(g, top, labels_out, s));
+    if (q_out) *q_out = q;
+    return CD_OK;
+}
+
+int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    CD_TRY(check_driver_params(p));
+    if (!labels_out) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule sched;
+    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level in;
+    CD_TRY(input_level(g, sc, &in));
+    uint32_t* dense;
+    CD_TRY(sc.get(&dense, in.n));
+    if (in.n > 0) {
+        uint32_t* lab;
+        int64_t sw = 0;
+        CD_TRY(local_move(in, p, CD_MODE_LPA, p->tolerance, sched, sc, dglob, s, &lab, &sw));
+        g_stats.sweeps = sw;
+        g_stats.passes = 1;
+        int64_t nc = 0;
+        CD_TRY(renumber_level(in, lab, dense, sc, dglob, &nc, s));
+        g_stats.communities = nc;
+    }
+    double q = 0.0;
+    CD_TRY(modularity_of(in, dense, sc, dglob, s, &q));
+    CD_TRY(emit_labels(g, dense, labels_out, s));
+    if (q_out) *q_out = q;
+    return CD_OK;
+}
+
 int cd_leiden(const cd_csr*, const cd_params*, uint32_t*, double*) { return CD_ENOTIMPL; }
-int cd_aggregate(const cd_csr*, const uint32_t*, void*, uint32_t*, int64_t*, int32_t*, uint32_t*, int64_t*,
-                 int64_t*) {
-    return CD_ENOTIMPL;
+
+int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t* dense_out,
+                 int64_t* offsets_out, int32_t* cols_out, uint32_t* weights_out, int64_t* n_out,
+                 int64_t* nnz_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    if (g->memory != CD_MEM_DEVICE) return CD_EINVAL;
+    if (!labels || !dense_out || !offsets_out || (g->nnz > 0 && (!cols_out || !weights_out)) || !n_out ||
+        !nnz_out)
+        return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level L;
+    CD_TRY(input_level(g, sc, &L));
+    int64_t nc = 0;
+    CD_TRY(renumber_level(L, labels, dense_out, sc, dglob, &nc, s));
+    Level next;
+    CD_TRY(aggregate_level(L, dense_out, nc, sc, dglob, s, offsets_out, cols_out, weights_out, &next));
+    CD_CUDA(cudaStreamSynchronize(s));
+    *n_out = next.n;
+    *nnz_out = next.nnz;
+    g_stats.communities = nc;
+    return CD_OK;
 }
 
 }  // extern "C"

@@ -25,6 +25,7 @@ struct Globals {
     unsigned long long sq_lo;    // modularity: sum_c Sigma_c^2
     unsigned long long sq_hi;
     unsigned long long count;    // generic counter (renumbering)
+    unsigned long long mark;     // movers before the current sub-sweep
     unsigned int err;            // nonzero: a device-side check failed
     unsigned int pad;
 };
@@ -65,12 +66,13 @@ cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int
                            uint64_t* K, Globals* glob, cudaStream_t s);
 cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,
                           uint32_t* size, Globals* glob, cudaStream_t s);
-// Bucketing: tile_counts / tile_offsets need nb * bucket_tiles(n) entries;
-// bucket_starts (nb + 1 int64) receives the first index of every bucket in
-// verts and the total.  Rows of length 0 are not listed; their label is
+// Bucketing by (colour class, bucket): tile_counts / tile_offsets need
+// colors * nb * bucket_tiles(n) entries; bucket_starts (colors * nb + 1 int64)
+// receives the first index of every (colour, bucket) range in verts and the
+// total.  Rows of length 0 are not listed; their label is
 // copied from labels_in to labels_out when labels_out is not null.
 int64_t bucket_tiles(int64_t n);
-cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt,
+cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
                           uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s);
@@ -78,6 +80,8 @@ cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblock
 cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in,
                           const uint32_t* labels_out, const uint64_t* K, int64_t n,
                           uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s);
+cudaError_t launch_copy_movers(const uint32_t* movers, const uint32_t* out, uint32_t* state, Globals* glob,
+                               int64_t n, cudaStream_t s);
 
 // sweep_exact.cu
 size_t exact_group_smem(int G, uint32_t T);
@@ -93,10 +97,40 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* cols, const uin
                               uint64_t* Sigma_scratch, uint32_t* sizes_scratch, Globals* glob,
                               cudaStream_t s);
 
+// scan.cu
+int64_t scan_tiles(int64_t n);
+cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n,
+                                      unsigned long long* tile_scratch, unsigned long long* total_dev,
+                                      cudaStream_t s);
+cudaError_t launch_exclusive_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n,
+                                             unsigned long long* tile_scratch, unsigned long long* total_dev,
+                                             cudaStream_t s);
+
+// aggregate.cu
+cudaError_t launch_renumber(const uint32_t* labels, int64_t n, uint32_t* dense, uint32_t* scratch_n,
+                            unsigned long long* tile_scratch, unsigned long long* count_dev, Globals* glob,
+                            cudaStream_t s);
+cudaError_t launch_compose(uint32_t* top, int64_t n0, const uint32_t* dense, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* x, int64_t n, cudaStream_t s);
+int64_t radix_tiles(int64_t n);
+struct AggScratch {
+    uint32_t *src, *dst, *w, *src2, *dst2, *w2, *hist, *heads;
+    unsigned long long *wsum, *tiles;
+};
+cudaError_t launch_expand(const int64_t* off, const int32_t* cols, int64_t n, int64_t nnz, const uint32_t* dense,
+                          uint32_t* src, uint32_t* dst, cudaStream_t s);
+cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* glob, cudaStream_t s);
+cudaError_t launch_heads(const AggScratch& a, int64_t nnz, cudaStream_t s);
+cudaError_t launch_segsum(const AggScratch& a, const uint32_t* uidx, int64_t nnz, int32_t* cols_out,
+                          uint32_t* rowcnt, cudaStream_t s);
+cudaError_t launch_narrow(const unsigned long long* wsum, int64_t m, uint32_t* w_out, Globals* glob,
+                          cudaStream_t s);
+
 // Device-side error flags (Globals::err bits).
 constexpr unsigned kErrBadOffsets = 1u;
 constexpr unsigned kErrBadCol = 2u;
 constexpr unsigned kErrZeroWeight = 4u;
 constexpr unsigned kErrBadLabel = 8u;
+constexpr unsigned kErrWeightOverflow = 16u;
 
 }  // namespace cdk

@@ -98,10 +98,12 @@ cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, 
 
 // ---------------------------------------------------------------------------
 // Degree bucketing.  Rows of length 0 never move (their label is copied);
-// the others are listed per bucket in ascending vertex id (stable), so that
-// neighbouring groups of a warp get rows of similar length.
+// the others are listed by (colour class, bucket) in ascending vertex id, so
+// that neighbouring groups of a warp get rows of similar length and every
+// colour class (one sub-sweep of the driver) is a contiguous range.
 // ---------------------------------------------------------------------------
 constexpr int kBucketTile = 2048;  // vertices per block, 8 rounds of 256
+constexpr int kMaxKeys = 256;      // colours x buckets
 
 __device__ __forceinline__ int bucket_of(int64_t deg, const BucketTable& bt) {
     if (deg == 0) return -1;
@@ -111,26 +113,50 @@ __device__ __forceinline__ int bucket_of(int64_t deg, const BucketTable& bt) {
     return bt.nb - 1;
 }
 
+// Colour class of vertex i among `colors` classes: the 32-bit integer hash
+// "lowbias32" (C. Wellons) of i, modulo the number of classes.
+__device__ __forceinline__ uint32_t color_of(uint32_t i, int colors) {
+    if (colors <= 1) return 0u;
+    uint32_t x = i;
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x % (uint32_t)colors;
+}
+
+__device__ __forceinline__ int key_of(const int64_t* __restrict__ off, int64_t v, int64_t n, int64_t nnz,
+                                      const BucketTable& bt, int colors, Globals* glob) {
+    int64_t o0 = off[v], o1 = off[v + 1];
+    bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
+    if (bad) {
+        if (glob) atomicOr(&glob->err, kErrBadOffsets);
+        return -1;
+    }
+    int b = bucket_of(o1 - o0, bt);
+    if (b < 0) return -1;
+    return (int)color_of((uint32_t)v, colors) * bt.nb + b;
+}
+
 int64_t bucket_tiles(int64_t n) { return (n + kBucketTile - 1) / kBucketTile; }
 
-__global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt,
+__global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt, int colors,
                                uint32_t* __restrict__ tile_counts, int64_t ntiles, Globals* glob) {
-    __shared__ uint32_t cnt[CD_MAX_BUCKETS];
-    if (threadIdx.x < CD_MAX_BUCKETS) cnt[threadIdx.x] = 0;
+    __shared__ uint32_t cnt[kMaxKeys];
+    const int nkeys = colors * bt.nb;
+    cnt[threadIdx.x] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * kBucketTile;
     for (int r = 0; r < kBucketTile / 256; ++r) {
         int64_t v = base + r * 256 + threadIdx.x;
         if (v < n) {
-            int64_t o0 = off[v], o1 = off[v + 1];
-            bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
-            if (bad) atomicOr(&glob->err, kErrBadOffsets);
-            int b = bad ? -1 : bucket_of(o1 - o0, bt);
-            if (b >= 0) atomicAdd(&cnt[b], 1u);
+            int key = key_of(off, v, n, nnz, bt, colors, glob);
+            if (key >= 0) atomicAdd(&cnt[key], 1u);
         }
     }
     __syncthreads();
-    if (threadIdx.x < bt.nb) tile_counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+    if ((int)threadIdx.x < nkeys) tile_counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
 // Single-block exclusive scan of a moderate array (tile counts); also writes
@@ -160,62 +186,63 @@ __global__ void k_scan_small(const uint32_t* __restrict__ in, uint32_t* __restri
 }
 
 __global__ void k_bucket_scatter(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt,
-                                 const uint32_t* __restrict__ tile_offsets, int64_t ntiles,
+                                 int colors, const uint32_t* __restrict__ tile_offsets, int64_t ntiles,
                                  uint32_t* __restrict__ verts, const uint32_t* __restrict__ labels_in,
                                  uint32_t* __restrict__ labels_out) {
-    __shared__ uint32_t wc[8][CD_MAX_BUCKETS];
-    __shared__ uint32_t run[CD_MAX_BUCKETS];
+    __shared__ uint32_t wc[8][kMaxKeys];
+    __shared__ uint32_t run[kMaxKeys];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < CD_MAX_BUCKETS) run[threadIdx.x] = 0;
+    run[threadIdx.x] = 0;
     int64_t base = (int64_t)blockIdx.x * kBucketTile;
     for (int r = 0; r < kBucketTile / 256; ++r) {
-        if (threadIdx.x < 8 * CD_MAX_BUCKETS) wc[threadIdx.x / CD_MAX_BUCKETS][threadIdx.x % CD_MAX_BUCKETS] = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) wc[q][threadIdx.x] = 0;
         __syncthreads();
         int64_t v = base + r * 256 + threadIdx.x;
-        int b = -1;
+        int key = -1;
         if (v < n) {
-            int64_t o0 = off[v], o1 = off[v + 1];
-            bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
-            b = bad ? -1 : bucket_of(o1 - o0, bt);
-            if (b < 0 && labels_out) labels_out[v] = labels_in[v];
+            key = key_of(off, v, n, nnz, bt, colors, nullptr);
+            if (key < 0 && labels_out) labels_out[v] = labels_in[v];
         }
-        unsigned peers = __match_any_sync(0xffffffffu, b);
+        unsigned peers = __match_any_sync(0xffffffffu, key);
         unsigned rank = __popc(peers & ((1u << lane) - 1u));
-        if (b >= 0 && rank == 0) wc[warp][b] = __popc(peers);
+        if (key >= 0 && rank == 0) wc[warp][key] = __popc(peers);
         __syncthreads();
-        if (b >= 0) {
-            uint32_t pos = tile_offsets[(int64_t)b * ntiles + blockIdx.x] + run[b] + rank;
-            for (int q = 0; q < warp; ++q) pos += wc[q][b];
+        if (key >= 0) {
+            uint32_t pos = tile_offsets[(int64_t)key * ntiles + blockIdx.x] + run[key] + rank;
+            for (int q = 0; q < warp; ++q) pos += wc[q][key];
             verts[pos] = (uint32_t)v;
         }
         __syncthreads();
-        if (threadIdx.x < CD_MAX_BUCKETS) {
-            uint32_t t = 0;
-            for (int q = 0; q < 8; ++q) t += wc[q][threadIdx.x];
-            run[threadIdx.x] += t;
-        }
+        uint32_t t = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += wc[q][threadIdx.x];
+        run[threadIdx.x] += t;
         __syncthreads();
     }
 }
 
-__global__ void k_bucket_starts(const uint32_t* __restrict__ tile_offsets, int64_t ntiles, int nb,
+__global__ void k_bucket_starts(const uint32_t* __restrict__ tile_offsets, int64_t ntiles, int nkeys,
                                 const unsigned long long* __restrict__ total, int64_t* __restrict__ starts) {
-    int b = threadIdx.x;
-    if (b < nb) starts[b] = tile_offsets[(int64_t)b * ntiles];
-    if (b == nb) starts[nb] = (int64_t)*total;
+    for (int b = threadIdx.x; b <= nkeys; b += blockDim.x) {
+        if (b < nkeys) starts[b] = tile_offsets[(int64_t)b * ntiles];
+        else starts[nkeys] = (int64_t)*total;
+    }
 }
 
-cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt,
+cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
                           uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s) {
-    if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (bt.nb + 1), s);
+    const int nkeys = colors * bt.nb;
+    if (nkeys > kMaxKeys) return cudaErrorInvalidValue;
+    if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (nkeys + 1), s);
     int64_t ntiles = bucket_tiles(n);
-    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, tile_counts, ntiles, glob);
-    k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, ntiles * bt.nb, &glob->count);
-    k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, tile_offsets, ntiles, verts,
+    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, tile_counts, ntiles, glob);
+    k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, ntiles * nkeys, &glob->count);
+    k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, tile_offsets, ntiles, verts,
                                                       labels_in, labels_out);
-    k_bucket_starts<<<1, 32, 0, s>>>(tile_offsets, ntiles, bt.nb, &glob->count, bucket_starts);
+    k_bucket_starts<<<1, 256, 0, s>>>(tile_offsets, ntiles, nkeys, &glob->count, bucket_starts);
     return cudaGetLastError();
 }
 
@@ -248,7 +275,7 @@ __global__ void k_commit(const uint32_t* __restrict__ movers, const uint32_t* __
                          unsigned long long* __restrict__ Sigma, uint32_t* __restrict__ size,
                          const Globals* __restrict__ glob) {
     const unsigned long long cnt = glob->moved;
-    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
+    for (unsigned long long t = glob->mark + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
          t += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t i = movers[t];
         uint32_t d = labels_in[i], c = labels_out[i];
@@ -269,6 +296,26 @@ cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in, con
     k_commit<<<(unsigned)blocks, 256, 0, s>>>(movers, labels_in, labels_out,
                                               (const unsigned long long*)K,
                                               (unsigned long long*)Sigma, size, glob);
+    return cudaGetLastError();
+}
+
+// state[i] = out[i] for the movers of the current sub-sweep ([mark, moved)).
+__global__ void k_copy_movers(const uint32_t* __restrict__ movers, const uint32_t* __restrict__ out,
+                              uint32_t* __restrict__ state, const Globals* __restrict__ glob) {
+    const unsigned long long cnt = glob->moved;
+    for (unsigned long long t = glob->mark + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t i = movers[t];
+        state[i] = out[i];
+    }
+}
+
+cudaError_t launch_copy_movers(const uint32_t* movers, const uint32_t* out, uint32_t* state, Globals* glob,
+                               int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_copy_movers<<<(unsigned)blocks, 256, 0, s>>>(movers, out, state, glob);
     return cudaGetLastError();
 }
 

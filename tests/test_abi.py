@@ -47,7 +47,7 @@ def test_struct_layout_matches_header(cd, tmp_path):
 int main(void) {
   printf("csr %zu %zu %zu\n", sizeof(cd_csr), offsetof(cd_csr, weights), offsetof(cd_csr, memory));
   printf("sched %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes));
-  printf("params %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing));
+  printf("params %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors));
   printf("stats %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, cuda_error));
   printf("parts %zu\n", sizeof(cd_modularity_parts));
   return 0;
@@ -59,7 +59,7 @@ int main(void) {
     exp = [
         f"csr {C.sizeof(cd.CSR)} {cd.CSR.weights.offset} {cd.CSR.memory.offset}",
         f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset}",
-        f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset}",
+        f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset}",
         f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.cuda_error.offset}",
         f"parts {C.sizeof(cd.ModularityParts)}",
     ]
@@ -99,15 +99,13 @@ def test_argument_checks_without_gpu(cd):
     assert rc(cd.make_params(k=8, schedule=bad_sched)) == cd.CD_EINVAL
     bad_sched = cd.schedule_from([4, 10**9], [1, 3])
     assert rc(cd.make_params(k=8, schedule=bad_sched)) == cd.CD_EINVAL
-    # host graph with an out-of-range column / zero weight / broken offsets
-    for mutate in ("col", "w", "off"):
+    # host graph with broken offsets (columns and weights are checked on the device)
+    for mutate in ("order", "end"):
         g2 = gen.sbm(50, 5, 0.3, 0.05, seed=1)
-        if mutate == "col":
-            g2.cols[3] = 50
-        elif mutate == "w":
-            g2.w[5] = 0
-        else:
+        if mutate == "order":
             g2.offsets[10] = g2.offsets[11] + 1
+        else:
+            g2.offsets[-1] += 1
         assert rc(cd.make_params(k=8), graph=cd.Graph.host(g2)) == cd.CD_EINVAL
     # labels out of range (host)
     lab2 = lab.copy()

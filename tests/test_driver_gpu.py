@@ -1,0 +1,136 @@
+"""Whole-algorithm parity: aggregation, Louvain and LPA drivers on the GPU
+(through the C ABI) against the oracle's twin of the same schedule, and the
+end-to-end modularity against the oracle's sequential run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_02268_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2411_02268_gb300 import _build
+    _build.build()
+    from paper_2411_02268_gb300 import cd
+    return cd, torch
+
+
+def sched_of(cd, k):
+    return oracle.Schedule(*cd.cd_default_schedule(k).as_lists())
+
+
+GRAPHS = {
+    "sbm10k": lambda: gen.sbm_10k(1),
+    "rmat13": lambda: gen.rmat(13, 16, wmax=16, seed=4),
+    "grid60": lambda: gen.grid(60, 60, 0.02, 16, seed=2),
+    "ragged_loops": lambda: gen.random_graph(500, 3000, 9, seed=8, self_loops=True),
+}
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+def test_aggregate_matches_oracle(env, gname):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    rng = np.random.default_rng(3)
+    for lab in (rng.integers(0, max(2, g.n // 9), g.n).astype(np.uint32),
+                (np.arange(g.n) // 7).astype(np.uint32), np.zeros(g.n, np.uint32),
+                np.arange(g.n, dtype=np.uint32)):
+        G = cd.Graph.to_device(g)
+        dense, G2 = cd.cd_aggregate(G, torch.from_numpy(lab.view(np.int32)).cuda())
+        R2, rdense = oracle.aggregate(g, lab)
+        assert np.array_equal(dense.cpu().numpy().view(np.uint32), rdense)
+        assert G2.n == R2.n
+        assert np.array_equal(G2.offsets.cpu().numpy(), R2.offsets)
+        assert np.array_equal(G2.cols.cpu().numpy(), R2.cols)
+        assert np.array_equal(G2.weights.cpu().numpy().view(np.uint32), R2.w)
+
+
+def test_aggregate_overflow_reported(env):
+    cd, torch = env
+    big = 2**31
+    g = gen.from_edges(3, [0, 1], [1, 2], [big, big])
+    G = cd.Graph.to_device(g)
+    with pytest.raises(cd.CDError) as ei:
+        cd.cd_aggregate(G, torch.zeros(3, dtype=torch.int32, device="cuda"))
+    assert ei.value.code == cd.CD_EOVERFLOW
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k,colors", [(8, 8), (0, 8), (4, 1), (16, 4)])
+def test_louvain_bit_exact_with_twin(env, gname, k, colors):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    G = cd.Graph.to_device(g)
+    p = cd.make_params(k=k, colors=colors, stream=torch.cuda.current_stream().cuda_stream)
+    lab, q = cd.cd_louvain(G, p)
+    got = lab.cpu().numpy().view(np.uint32)
+    ref = oracle.louvain_sync(g, k=k, sched=sched_of(cd, k), threads=8, colors=colors)
+    assert np.array_equal(got, ref)
+    assert q == pytest.approx(float(oracle.modularity_fraction(g, ref)), abs=1e-15)
+    st = cd.cd_last_stats()
+    assert st.communities == len(np.unique(ref)) and st.passes >= 1
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k,colors", [(8, 8), (0, 8), (8, 1)])
+def test_lpa_bit_exact_with_twin(env, gname, k, colors):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    G = cd.Graph.to_device(g)
+    p = cd.make_params(k=k, colors=colors, tolerance=0.05)
+    lab, q = cd.cd_lpa(G, p)
+    got = lab.cpu().numpy().view(np.uint32)
+    ref = oracle.lpa_sync(g, k=k, sched=sched_of(cd, k), threads=8, colors=colors)
+    assert np.array_equal(got, ref)
+    assert q == pytest.approx(float(oracle.modularity_fraction(g, ref)), abs=1e-15)
+
+
+@pytest.mark.parametrize("gname", ["sbm10k", "rmat13", "grid60"])
+@pytest.mark.parametrize("k", [0, 8])
+def test_louvain_modularity_within_tolerance_of_sequential(env, gname, k):
+    """End to end with concurrent moves: final Q within 0.005 of (or above)
+    the oracle's sequential Gauss-Seidel Louvain."""
+    cd, torch = env
+    g = GRAPHS[gname]()
+    _, q = cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=k))
+    qs = oracle.modularity(g, oracle.louvain_seq(g, k=k))
+    assert q >= qs - 0.005, (q, qs)
+    assert -0.5 <= q <= 1.0
+
+
+def test_louvain_host_memory_and_invariants(env):
+    cd, torch = env
+    g = GRAPHS["rmat13"]()
+    lab_h, q_h = cd.cd_louvain(cd.Graph.host(g), cd.make_params(k=8))
+    lab_d, q_d = cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=8))
+    assert np.array_equal(np.asarray(lab_h), lab_d.cpu().numpy().view(np.uint32))
+    assert q_h == q_d
+    # dense ids
+    u = np.unique(lab_h)
+    assert u[0] == 0 and u[-1] == len(u) - 1
+
+
+def test_louvain_two_triangles(env):
+    cd, torch = env
+    g = gen.from_edges(6, [0, 0, 1, 2, 3, 3, 4], [1, 2, 2, 3, 4, 5, 5], [1] * 7)
+    for k in (0, 8):
+        lab, q = cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=k, tolerance=0.0))
+        assert q == pytest.approx(5 / 14, abs=1e-15)
+        l = lab.cpu().numpy()
+        assert len(set(l[:3])) == 1 and len(set(l[3:])) == 1 and l[0] != l[3]
+
+
+def test_degenerate_driver_inputs(env):
+    cd, torch = env
+    empty = gen.from_edges(4, [], [], [])
+    lab, q = cd.cd_louvain(cd.Graph.to_device(empty), cd.make_params(k=8))
+    assert lab.cpu().numpy().tolist() == [0, 1, 2, 3] and q == 0.0
+    lab, q = cd.cd_lpa(cd.Graph.to_device(empty), cd.make_params(k=8))
+    assert lab.cpu().numpy().tolist() == [0, 1, 2, 3]
+    with pytest.raises(cd.CDError):
+        cd.cd_louvain(cd.Graph.to_device(empty), cd.make_params(k=8, tolerance_drop=0.5))

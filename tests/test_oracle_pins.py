@@ -392,3 +392,48 @@ def test_lpa_converges_on_cliques():
     g = gen.from_edges(24, src, dst, w + [1, 1, 1])
     lab = oracle.lpa_seq(g, k=8, tol=0.0)
     assert len(np.unique(lab)) == 4
+
+
+def _lowbias32(x: int) -> int:
+    x &= 0xFFFFFFFF
+    x ^= x >> 16
+    x = (x * 0x7FEB352D) & 0xFFFFFFFF
+    x ^= x >> 15
+    x = (x * 0x846CA68B) & 0xFFFFFFFF
+    x ^= x >> 16
+    return x
+
+
+def test_color_classes_follow_lowbias32():
+    n, P = 5000, 8
+    c = oracle.color_classes(n, P)
+    assert [int(v) for v in c[:300]] == [_lowbias32(i) % P for i in range(300)]
+    assert int(c[4999]) == _lowbias32(4999) % P
+    counts = np.bincount(c, minlength=P)
+    assert counts.min() > 0.8 * n / P
+    assert np.all(oracle.color_classes(10, 1) == 0)
+
+
+@pytest.mark.parametrize("colors", [1, 2, 8])
+def test_sync_louvain_invariants(colors):
+    g = gen.sbm(600, 12, 0.15, 0.005, wmax=5, seed=6)
+    lab = oracle.louvain_sync(g, k=8, colors=colors, threads=2)
+    u = np.unique(lab)
+    assert u[0] == 0 and u[-1] == len(u) - 1
+    q = oracle.modularity_fraction(g, lab)
+    assert Fraction(-1, 2) <= q <= 1
+    # colour classes tame synchronous oscillation: at least as good as P=1
+    if colors == 8:
+        q1 = oracle.modularity_fraction(g, oracle.louvain_sync(g, k=8, colors=1, threads=2))
+        assert q >= q1 - Fraction(1, 100)
+
+
+def test_sync_louvain_below_brute_force():
+    for seed in range(4):
+        g = gen.random_graph(8, 14, 4, seed=700 + seed)
+        if g.nnz == 0:
+            continue
+        qstar, _ = oracle.brute_force_best(g)
+        for colors in (1, 8):
+            lab = oracle.louvain_sync(g, k=8, colors=colors, tol=0.0)
+            assert oracle.modularity_fraction(g, lab) <= qstar

@@ -222,6 +222,26 @@ def test_device_detects_bad_columns(env):
     assert ei.value.code == cd.CD_EINVAL
 
 
+@pytest.mark.parametrize("mutate", ["col", "w"])
+@pytest.mark.parametrize("host", [False, True])
+def test_bad_columns_and_weights_rejected(env, mutate, host):
+    cd, torch = env
+    g = gen.sbm(300, 5, 0.2, 0.02, seed=2)
+    if mutate == "col":
+        g.cols[3] = 300
+    else:
+        g.w[5] = 0
+    G = cd.Graph.host(g) if host else cd.Graph.to_device(g)
+    lab = np.arange(g.n, dtype=np.uint32)
+    lab = lab if host else torch.from_numpy(lab.view(np.int32)).cuda()
+    for k in (8, 0):
+        with pytest.raises(cd.CDError) as ei:
+            cd.cd_sweep(G, cd.make_params(k=k), 0, lab)
+        assert ei.value.code == cd.CD_EINVAL
+    with pytest.raises(cd.CDError):
+        cd.cd_louvain(G, cd.make_params(k=8))
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_modularity_parity(env, seed):
     cd, torch = env
