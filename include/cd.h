@@ -50,6 +50,7 @@ extern "C" {
 #define CD_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define CD_EOVERFLOW (-5) /* a weight sum does not fit the integer type */
 #define CD_ENOTIMPL (-6)  /* entry point or option not available */
+#define CD_ESIZE (-7)     /* input larger than an entry point's fixed scratch holds */
 
 /* sweep modes */
 #define CD_MODE_LOUVAIN 0 /* delta-modularity, Eq. 2 (Section 3.3, 4.1) */
@@ -198,6 +199,30 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
 int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t* dense_out,
                  int64_t* offsets_out, int32_t* cols_out, uint32_t* weights_out,
                  int64_t* n_out, int64_t* nnz_out);
+
+/*
+ * Modularity without any device allocation.  The paper has no counterpart:
+ * this is an interface for callers that cannot allocate device memory while
+ * they call the library - for example code whose device memory is owned by a
+ * framework's caching allocator (a raw cudaMalloc/cudaFree there would
+ * synchronise the device or fragment the pool), or services that must keep a
+ * fixed device-memory budget.  It computes exactly what cd_modularity
+ * computes (same kernels, same integer parts), but its scratch (weighted
+ * degrees, community totals and sizes of up to 2^20 vertices, 20 MiB plus
+ * 256 bytes) is one fixed array inside the library, which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture on the device.  All calls share the array and each call starts by
+ * clearing what it reads: calls whose work overlaps on the GPU (several
+ * streams, several host threads) race on it and must be serialised by the
+ * caller.  Device memory only (CD_EINVAL for CD_MEM_HOST); n > 2^20 returns
+ * CD_ESIZE.  Other arguments and results as cd_modularity; the call
+ * synchronises `stream`.
+ */
+int cd_modularity_noalloc(const cd_csr* g, const uint32_t* labels, void* stream, double* q_out,
+                          cd_modularity_parts* parts);
 
 #ifdef __cplusplus
 }

@@ -17,14 +17,14 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(_PKG, "lib", "libcd.so")
 
-CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_EOVERFLOW, CD_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_EOVERFLOW, CD_ENOTIMPL, CD_ESIZE = 0, -1, -2, -3, -4, -5, -6, -7
 MODE_LOUVAIN, MODE_LPA, MODE_REFINE = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 MAX_BUCKETS = 16
 
 # Symbols declared in include/cd.h.
 SYMBOLS = ("cd_strerror", "cd_last_stats", "cd_default_schedule", "cd_sweep", "cd_modularity",
-           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate")
+           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_modularity_noalloc")
 
 
 class CSR(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib():
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64)]
             L.cd_modularity.argtypes = [ctypes.POINTER(CSR), P, P, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ModularityParts)]
+            L.cd_modularity_noalloc.argtypes = L.cd_modularity.argtypes
             for name in ("cd_louvain", "cd_lpa", "cd_leiden"):
                 getattr(L, name).argtypes = [ctypes.POINTER(CSR), ctypes.POINTER(Params), P,
                                              ctypes.POINTER(ctypes.c_double)]
@@ -226,6 +227,18 @@ def cd_modularity(g: Graph, labels, stream=None):
     st = stream.value if isinstance(stream, ctypes.c_void_p) else stream
     _check(lib().cd_modularity(ctypes.byref(csr), _ptr(labels), st, ctypes.byref(q), ctypes.byref(parts)),
            "cd_modularity")
+    return q.value, (parts.sigma_in, parts.sum_sq_lo | (parts.sum_sq_hi << 64), parts.two_m)
+
+
+def cd_modularity_noalloc(g: Graph, labels, stream=None):
+    """As cd_modularity, with the library's fixed scratch array instead of any
+    device allocation (device memory only, at most 2^20 vertices)."""
+    q = ctypes.c_double()
+    parts = ModularityParts()
+    csr = g.csr()
+    st = stream.value if isinstance(stream, ctypes.c_void_p) else stream
+    _check(lib().cd_modularity_noalloc(ctypes.byref(csr), _ptr(labels), st, ctypes.byref(q), ctypes.byref(parts)),
+           "cd_modularity_noalloc")
     return q.value, (parts.sigma_in, parts.sum_sq_lo | (parts.sum_sq_hi << 64), parts.two_m)
 
 

@@ -500,6 +500,15 @@ int emit_labels(const cd_csr* g, const uint32_t* dense, uint32_t* labels_out, cu
 
 }  // namespace
 
+namespace cdk {
+// Records a CUDA error string in the calling thread's statistics.
+void record_cuda_error(cudaError_t e) {
+    reset_stats();
+    std::snprintf(g_stats.cuda_error, sizeof(g_stats.cuda_error), "%s", cudaGetErrorString(e));
+    cudaGetLastError();
+}
+}  // namespace cdk
+
 extern "C" {
 
 const char* cd_strerror(int code) {
@@ -511,6 +520,7 @@ const char* cd_strerror(int code) {
         case CD_ETIMEOUT: return "device wait timed out";
         case CD_EOVERFLOW: return "integer overflow";
         case CD_ENOTIMPL: return "not implemented";
+        case CD_ESIZE: return "input exceeds the fixed scratch of this entry point";
         default: return "unknown status";
     }
 }
