@@ -107,7 +107,12 @@ typedef struct cd_params {
     int32_t colors;       /* drivers: each sweep is `colors` sub-sweeps, sub-sweep p deciding
                              the vertices i with lowbias32(i) mod colors = p from the state
                              left by the previous sub-sweeps (1 = fully synchronous sweeps,
-                             0 = default 8, at most 16); cd_sweep ignores it */
+                             0 = default 8, at most 16); cd_sweep uses it in refine mode */
+    int32_t sub_color;    /* cd_sweep, refine mode: the colour class deciding in this sweep
+                             (pass the vertices of that class as `active`) */
+    int32_t one_scan;     /* LPA only (cd_sweep mode LPA, cd_lpa): the "1-scan" variant of
+                             Section 4.3, deciding on the sketch values without the second
+                             scan (needs k > 0) */
 } cd_params;
 
 typedef struct cd_stats {

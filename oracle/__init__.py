@@ -73,7 +73,8 @@ def _load():
             lib.or_sketch_merge.argtypes = [_p, _p, _p, _p, ctypes.c_int, ctypes.c_int]
             lib.or_sweep.argtypes = ([_i64, _p, _p, _p, _p, _p, _p, _p, ctypes.c_uint64, _p, _p,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _p, _p,
-                                      ctypes.c_int, _i64, _i64, _p, _p, _p])
+                                      ctypes.c_int, _i64, _i64, _p, _p, _p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int])
             lib.or_row_sketch.argtypes = [_i64, _p, _p, _p, _p, _p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, _p, _p, ctypes.c_int, _p, _p]
             lib.or_local_move_seq.argtypes = [_i64, _p, _p, _p, _p, ctypes.c_int, ctypes.c_int,
@@ -196,7 +197,7 @@ def row_sketch(g, i: int, labels, k: int, sched: Schedule, uncond=False, bound=N
 
 def sweep(g, labels, mode: int = MODE_LOUVAIN, k: int = 8, uncond: bool = False,
           sched: Schedule | None = None, active=None, bound=None, vertices=None,
-          threads: int = 1, state=None):
+          threads: int = 1, state=None, colors: int = 1, sub_color: int = 0, one_scan: bool = False):
     """One synchronous sweep from `labels` (see or_sweep in oracle.c).
 
     Returns (labels_out, gains) where gains is an object array of Python ints
@@ -227,7 +228,7 @@ def sweep(g, labels, mode: int = MODE_LOUVAIN, k: int = 8, uncond: bool = False,
         lib.or_sweep(n, _ptr(off), _ptr(cols), _ptr(w), _ptr(labels), _ptr(K), _ptr(Sig),
                      _ptr(size), two_m, _ptr(bnd), _ptr(act), mode, k, int(uncond),
                      len(sched.lanes), _ptr(sched.deg_max), _ptr(sched.lanes), sched.vec,
-                     a, b, _ptr(out), _ptr(glo), _ptr(ghi))
+                     a, b, _ptr(out), _ptr(glo), _ptr(ghi), colors, sub_color, int(one_scan))
 
     if threads <= 1 or v1 - v0 < 1024:
         run(v0, v1)
@@ -380,7 +381,8 @@ def color_classes(n: int, colors: int) -> np.ndarray:
     return x % np.uint32(colors)
 
 
-def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, colors=8):
+def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, colors=8, init=None,
+                    one_scan=False):
     """Local-moving phase from singletons, each sweep made of `colors`
     sub-sweeps: sub-sweep p decides the vertices of colour class p, all at
     once, from the state left by the previous sub-sweeps (colors=1: fully
@@ -388,7 +390,7 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
     summed delta-Q is <= tol (Louvain) or at most tol * n labels changed
     (LPA), or after max_sweeps.  Returns (labels, sweeps)."""
     n = g.n
-    labels = np.arange(n, dtype=np.uint32)
+    labels = np.arange(n, dtype=np.uint32) if init is None else np.array(init, dtype=np.uint32)
     K = degrees(g)
     two_m = int(K.sum(dtype=np.uint64))
     col = color_classes(n, colors)
@@ -399,7 +401,7 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
         for act in masks:
             Sig, size = community_totals(n, labels, K)
             out, gains = sweep(g, labels, mode, k, uncond, sched, active=act if colors > 1 else None,
-                               threads=threads, state=(K, Sig, size, two_m))
+                               threads=threads, state=(K, Sig, size, two_m), one_scan=one_scan)
             moved += int(np.count_nonzero(out != labels))
             gsum += gain_total(gains)
             labels = out
@@ -433,8 +435,60 @@ def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, m
     return top
 
 
-def lpa_sync(g, k=8, uncond=False, tol=0.05, max_sweeps=20, sched=None, threads=1, colors=8):
+def lpa_sync(g, k=8, uncond=False, tol=0.05, max_sweeps=20, sched=None, threads=1, colors=8,
+             one_scan=False):
     """LPA with colour-class sub-sweeps: the exact schedule of cd_lpa."""
     sched = sched or Schedule.single_stream()
-    lab, _ = local_move_sync(g, MODE_LPA, k, uncond, tol, max_sweeps, sched, threads, colors)
+    lab, _ = local_move_sync(g, MODE_LPA, k, uncond, tol, max_sweeps, sched, threads, colors,
+                             one_scan=one_scan)
     return renumber(lab)[0]
+
+
+def refine_sync(g, bound, k=8, uncond=False, sched=None, threads=1, colors=8):
+    """Leiden refinement (Section 3.4): sub-communities start as singletons;
+    one sweep of `colors` sub-sweeps in refine mode: only vertices still in
+    a singleton move, only to sub-communities inside their own bound, and a
+    same-colour singleton is never a target.  Returns sub-community labels."""
+    sched = sched or Schedule.single_stream()
+    n = g.n
+    labels = np.arange(n, dtype=np.uint32)
+    K = degrees(g)
+    two_m = int(K.sum(dtype=np.uint64))
+    bound = np.ascontiguousarray(bound, dtype=np.uint32)
+    col = color_classes(n, colors)
+    for p in range(colors):
+        Sig, size = community_totals(n, labels, K)
+        labels, _ = sweep(g, labels, MODE_REFINE, k, uncond, sched, active=(col == p).astype(np.uint8),
+                          bound=bound, threads=threads, state=(K, Sig, size, two_m), colors=colors, sub_color=p)
+    return labels
+
+
+def leiden_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
+                agg_tol=0.8, sched=None, threads=1, colors=8):
+    """Leiden (Section 3.4): local-moving (from the previous level's bounds),
+    refinement within the communities found, aggregation by the refined
+    partition, repeated; the result is the last level's communities mapped
+    to the input vertices.  The exact schedule of cd_leiden."""
+    sched = sched or Schedule.single_stream()
+    top = np.arange(g.n, dtype=np.uint32)
+    result = top.copy()
+    cur, init = g, None
+    for p in range(max_passes):
+        if cur.n == 0:
+            break
+        lab, _ = local_move_sync(cur, MODE_LOUVAIN, k, uncond, tol, max_sweeps, sched, threads, colors, init)
+        dc, nc = renumber(lab)
+        result = dc[top]
+        if nc == cur.n or p + 1 >= max_passes:
+            break
+        rl = refine_sync(cur, dc, k, uncond, sched, threads, colors)
+        dr, nr = renumber(rl)
+        if nr == cur.n or nr > agg_tol * cur.n:
+            break
+        nxt = np.empty(nr, dtype=np.uint32)
+        nxt[dr] = dc
+        top = dr[top]
+        cur, _ = aggregate(cur, dr)
+        init = nxt
+        tol /= tol_drop
+    return renumber(result)[0]

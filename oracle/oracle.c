@@ -177,6 +177,19 @@ static uint64_t link_weight(int64_t i, uint32_t c, const int64_t* off, const int
     return s;
 }
 
+/* Colour class of vertex v among `colors` classes: the 32-bit integer hash
+ * "lowbias32" (C. Wellons) of v, modulo the number of classes. */
+static uint32_t color_of(uint32_t v, int colors) {
+    if (colors <= 1) return 0u;
+    uint32_t x = v;
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x % (uint32_t)colors;
+}
+
 /* Scaled delta-modularity, Eq. 2 multiplied by 2m^2:
  *   gain = 2m (K_{i->c} - K_{i->d}) - K_i (K_i + Sigma_c - Sigma_d). */
 static i128 dq_gain(uint64_t two_m, uint64_t Kic, uint64_t Kid, uint64_t Ki, uint64_t Sc, uint64_t Sd) {
@@ -195,8 +208,13 @@ static i128 dq_gain(uint64_t two_m, uint64_t Kic, uint64_t Kid, uint64_t Ki, uin
  * singleton community with a larger id (stops pairwise swaps in a synchronous
  * sweep); best gain wins, ties to the smaller id; moves iff gain > 0.
  * LPA: largest K_{i->c} wins, ties to the smaller id; moves iff it exceeds
- * K_{i->d}.  The refine mode restricts both scans to bound[j] == bound[i] and
- * moves only vertices whose community is a singleton.
+ * K_{i->d}.
+ * Refine (Leiden, Section 3.4): both scans are restricted to neighbours with
+ * bound[j] == bound[i]; only vertices whose community is a singleton move;
+ * the singleton rule above is replaced by: a singleton community whose
+ * vertex has colour `sub_color` (the colour class deciding in this
+ * sub-sweep, among `colors`) is not a candidate, so that no vertex joins a
+ * community whose only member may leave in the same sub-sweep.
  *
  * Vertices in [v0, v1) with active[i] != 0 (or all, active == NULL) are
  * decided; the others copy their label.  gains_out (optional) receives the
@@ -206,7 +224,8 @@ void or_sweep(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t
               const uint32_t* labels, const uint64_t* K, const uint64_t* Sigma, const uint32_t* size,
               uint64_t two_m, const uint32_t* bound, const uint8_t* active, int mode, int k, int uncond,
               int nbuckets, const int64_t* deg_max, const int32_t* lanes, int vec,
-              int64_t v0, int64_t v1, uint32_t* labels_out, uint64_t* gain_lo, uint64_t* gain_hi) {
+              int64_t v0, int64_t v1, uint32_t* labels_out, uint64_t* gain_lo, uint64_t* gain_hi,
+              int colors, int sub_color, int one_scan) {
     or_sched sched = {nbuckets, deg_max, lanes, vec};
     (void)n;
     int kk = k > 0 ? k : 1;
@@ -242,20 +261,36 @@ void or_sweep(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t
                 if (!seen) cand[ncand++] = c;
             }
         }
-        uint64_t Kid = link_weight(i, d, off, cols, w, labels, bnd);
+        /* LPA 1-scan variant (Section 4.3): the sketch values stand in for the
+         * linking weights and no second scan is made */
+        const int sketch_weights = one_scan && k > 0 && mode == MODE_LPA;
+        uint64_t Kid = 0;
+        if (sketch_weights) {
+            for (int p = 0; p < k; ++p)
+                if (keys[p] == d) Kid = vals[p];
+        } else {
+            Kid = link_weight(i, d, off, cols, w, labels, bnd);
+        }
         uint32_t best = d;
         i128 best_gain = 0;
         uint64_t best_k = Kid;
         int have = 0;
         for (int64_t q = 0; q < ncand; ++q) {
             uint32_t c = cand[q];
-            uint64_t Kic = link_weight(i, c, off, cols, w, labels, bnd);
+            uint64_t Kic = 0;
+            if (sketch_weights) {
+                for (int p = 0; p < k; ++p)
+                    if (keys[p] == c) Kic = vals[p];
+            } else {
+                Kic = link_weight(i, c, off, cols, w, labels, bnd);
+            }
             if (mode == MODE_LPA) {
                 if (Kic > Kid && (Kic > best_k || (Kic == best_k && c < best))) {
                     best = c; best_k = Kic; have = 1;
                 }
             } else {
                 if (mode == MODE_LOUVAIN && size[d] == 1 && size[c] == 1 && c > d) continue;
+                if (mode == MODE_REFINE && size[c] == 1 && (int)color_of(c, colors) == sub_color) continue;
                 i128 g = dq_gain(two_m, Kic, Kid, K[i], Sigma[c], Sigma[d]);
                 if (g > 0 && (g > best_gain || (g == best_gain && c < best))) {
                     best = c; best_gain = g; have = 1;

@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("tolerance_drop", ctypes.c_double), ("aggregation_tolerance", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("sched", ctypes.POINTER(Schedule)), ("stream", ctypes.c_void_p),
-                ("timing", ctypes.c_int32), ("colors", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("colors", ctypes.c_int32),
+                ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -163,7 +164,7 @@ def current_stream():
 
 def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregation_tolerance=0.8,
                 max_sweeps=20, max_passes=10, schedule: Schedule | None = None, stream=None,
-                timing=False, colors=0) -> Params:
+                timing=False, colors=0, sub_color=0, one_scan=False) -> Params:
     p = Params()
     p.k, p.subtract = int(k), int(subtract)
     p.tolerance, p.tolerance_drop, p.aggregation_tolerance = tolerance, tolerance_drop, aggregation_tolerance
@@ -172,6 +173,8 @@ def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregatio
     p.stream = stream.value if isinstance(stream, ctypes.c_void_p) else stream
     p.timing = int(bool(timing))
     p.colors = int(colors)
+    p.sub_color = int(sub_color)
+    p.one_scan = int(bool(one_scan))
     p._keep = schedule
     return p
 

@@ -71,6 +71,21 @@ cudaError_t launch_iota(uint32_t* x, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// next_init[sub[v]] = bound[v]: the community of every sub-community (all
+// members of a sub-community share one bound, so the writes agree).
+__global__ void k_scatter_bound(const uint32_t* __restrict__ sub, const uint32_t* __restrict__ bound, int64_t n,
+                                uint32_t* __restrict__ next_init) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < n) next_init[sub[v]] = bound[v];
+}
+
+cudaError_t launch_scatter_bound(const uint32_t* sub, const uint32_t* bound, int64_t n, uint32_t* next_init,
+                                 cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_scatter_bound<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sub, bound, n, next_init);
+    return cudaGetLastError();
+}
+
 // ---- super-vertex graph ----------------------------------------------------------
 
 constexpr int kExpandChunk = 64;

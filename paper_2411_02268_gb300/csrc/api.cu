@@ -111,6 +111,8 @@ int check_params(const cd_params* p) {
     if (!p) return CD_EINVAL;
     if (!(p->k == 0 || p->k == 1 || p->k == 2 || p->k == 4 || p->k == 8 || p->k == 16)) return CD_EINVAL;
     if (p->subtract != 0 && p->subtract != 1) return CD_EINVAL;
+    if (p->one_scan != 0 && p->one_scan != 1) return CD_EINVAL;
+    if (p->one_scan && p->k == 0) return CD_EINVAL;
     if (p->sched) CD_TRY(check_schedule(p->sched));
     return CD_OK;
 }
@@ -228,13 +230,15 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
 }
 
 SweepArgs make_args(const Level& L, const uint32_t* labels_in, uint32_t* labels_out, const uint8_t* active,
-                    const uint32_t* bound, Globals* dglob, int mode, int uncond) {
+                    const uint32_t* bound, Globals* dglob, int mode, int uncond, int colors = 1, int sub_color = 0) {
     SweepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.off = L.off; a.cols = L.cols; a.w = L.w;
     a.labels = labels_in; a.K = L.K; a.Sigma = L.Sigma; a.size = L.size;
     a.active = active; a.bound = bound; a.labels_out = labels_out; a.movers = L.movers;
     a.glob = dglob; a.verts = L.verts; a.n = L.n; a.nnz = L.nnz; a.mode = mode; a.uncond = uncond;
+    a.colors = colors; a.sub_color = sub_color;
+    a.one_scan = 0;
     a.bt = L.bt;
     return a;
 }
@@ -380,17 +384,24 @@ double gain_as_double(unsigned long long lo, unsigned long long hi) {
 // by the commit into Sigma and sizes) until nobody moves, the sweep's summed
 // delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
 // max_sweeps.  Returns the final labels in *labels (one of two scratch buffers).
+int resolve_colors(const cd_params* p) { return p->colors == 0 ? 8 : p->colors; }
+
+// Local-moving phase on level L from `init` labels (singletons when null):
+// every sweep is `colors` sub-sweeps (sub-sweep c decides the vertices of
+// colour class c from the state left by the previous ones), each followed by
+// the commit into Sigma and sizes, until nobody moves, the sweep's summed
+// delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
+// max_sweeps.  Returns the final labels in *labels (a scratch buffer).
 int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_schedule& sched, Scratch& sc,
-               Globals* dglob, cudaStream_t s, uint32_t** labels, int64_t* sweeps_out) {
+               Globals* dglob, cudaStream_t s, const uint32_t* init, uint32_t** labels, int64_t* sweeps_out) {
     uint32_t *la, *lb;
     CD_TRY(sc.get(&la, L.n));
     CD_TRY(sc.get(&lb, L.n));
     CD_TRY(sc.get(&L.movers, L.n));
-    CD_CUDA(launch_iota(la, L.n, s));
-    const int colors = p->colors == 0 ? 8 : p->colors;
+    if (init) CD_CUDA(cudaMemcpyAsync(la, init, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
+    else CD_CUDA(launch_iota(la, L.n, s));
+    const int colors = resolve_colors(p);
     CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
-    // both label buffers hold every vertex: copy the rows of length 0 as well
-    CD_CUDA(cudaMemcpyAsync(lb, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
     std::vector<Timer> tms((size_t)colors);
     for (auto& t : tms) CD_TRY(t.init(p->timing != 0));
     const size_t stat_off = offsetof(Globals, moved);
@@ -399,18 +410,18 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     for (; sw < p->max_sweeps;) {
         CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
         for (int c = 0; c < colors; ++c) {
-            // sub-sweep c: vertices of colour c decide from la; the others keep
-            // their label in lb, which then becomes the state of sub-sweep c+1
+            // sub-sweep c: vertices of colour c decide from la and write lb; the
+            // movers' new labels are then copied into la for sub-sweep c+1
             CD_CUDA(cudaMemcpyAsync(&dglob->mark, &dglob->moved, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToDevice, s));
             Level Lc = L;
             Lc.bt = L.table_for(c);
             SweepArgs a = make_args(Lc, la, lb, nullptr, nullptr, dglob, mode, p->subtract);
+            a.one_scan = p->one_scan;
             if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].a, s));
             CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
             if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, s));
             CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
-            // carry the moves of this sub-sweep into la for the next one
             CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
         }
         HostGlobals hg;
@@ -437,6 +448,39 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     }
     *labels = la;
     *sweeps_out = sw;
+    return CD_OK;
+}
+
+// Leiden refinement (Section 3.4, 4.2) of level L within the communities
+// `bound`: sub-communities start as singletons; one sweep of `colors`
+// sub-sweeps in refine mode (only singletons move, only inside their bound,
+// never into a same-colour singleton).  Returns the sub-community labels.
+int refine_level(Level& L, const cd_params* p, const uint32_t* bound, const cd_schedule& sched, Scratch& sc,
+                 Globals* dglob, cudaStream_t s, uint32_t** labels) {
+    uint32_t *la, *lb;
+    CD_TRY(sc.get(&la, L.n));
+    CD_TRY(sc.get(&lb, L.n));
+    CD_TRY(sc.get(&L.movers, L.n));
+    CD_CUDA(launch_iota(la, L.n, s));
+    const int colors = resolve_colors(p);
+    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
+    const size_t stat_off = offsetof(Globals, moved);
+    const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
+    CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
+    for (int c = 0; c < colors; ++c) {
+        CD_CUDA(cudaMemcpyAsync(&dglob->mark, &dglob->moved, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, s));
+        Level Lc = L;
+        Lc.bt = L.table_for(c);
+        SweepArgs a = make_args(Lc, la, lb, nullptr, bound, dglob, CD_MODE_REFINE, p->subtract, colors, c);
+        CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
+        CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
+        CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
+    }
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    g_stats.sweeps += 1;
+    *labels = la;
     return CD_OK;
 }
 
@@ -543,7 +587,10 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     reset_stats();
     CD_TRY(check_csr(g));
     CD_TRY(check_params(p));
-    if (mode != CD_MODE_LOUVAIN && mode != CD_MODE_LPA) return mode == CD_MODE_REFINE ? CD_ENOTIMPL : CD_EINVAL;
+    if (mode != CD_MODE_LOUVAIN && mode != CD_MODE_LPA && mode != CD_MODE_REFINE) return CD_EINVAL;
+    if ((mode == CD_MODE_REFINE) != (bound != nullptr)) return CD_EINVAL;
+    if (p->one_scan && mode != CD_MODE_LPA) return CD_EINVAL;
+    if (p->colors < 0 || p->colors > 16 || p->sub_color < 0 || p->sub_color >= resolve_colors(p)) return CD_EINVAL;
     if (!labels_in || !labels_out || labels_in == labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
@@ -568,6 +615,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         CD_TRY(stage_in(labels_in, g->n, &li, sc));
         CD_TRY(sc.get(&lout, g->n));
         if (active) { uint8_t* da; CD_TRY(stage_in(active, g->n, &da, sc)); act = da; }
+        if (bound) { uint32_t* db; CD_TRY(stage_in(bound, g->n, &db, sc)); bound = db; }
         L.off = off; L.cols = cols; L.w = w; lin = li;
     } else {
         L.off = g->offsets; L.cols = g->cols; L.w = g->weights;
@@ -580,7 +628,8 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         return CD_OK;
     }
     CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, 1, sc, dglob, s));
-    SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract);
+    SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, resolve_colors(p), p->sub_color);
+    a.one_scan = p->one_scan;
     Timer tm;
     CD_TRY(tm.init(p->timing != 0));
     if (tm.on) CD_CUDA(cudaEventRecord(tm.a, s));
@@ -662,6 +711,7 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
     reset_stats();
     CD_TRY(check_csr(g));
     CD_TRY(check_driver_params(p));
+    if (p->one_scan) return CD_EINVAL;
     if (!labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
@@ -680,7 +730,7 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
     for (int pass = 0; pass < p->max_passes && cur.n > 0; ++pass) {
         uint32_t* lab;
         int64_t sw = 0;
-        CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, &lab, &sw));
+        CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, nullptr, &lab, &sw));
         g_stats.sweeps += sw;
         g_stats.passes += 1;
         uint32_t* dense;
@@ -722,7 +772,7 @@ int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_
     if (in.n > 0) {
         uint32_t* lab;
         int64_t sw = 0;
-        CD_TRY(local_move(in, p, CD_MODE_LPA, p->tolerance, sched, sc, dglob, s, &lab, &sw));
+        CD_TRY(local_move(in, p, CD_MODE_LPA, p->tolerance, sched, sc, dglob, s, nullptr, &lab, &sw));
         g_stats.sweeps = sw;
         g_stats.passes = 1;
         int64_t nc = 0;
@@ -736,7 +786,71 @@ int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_
     return CD_OK;
 }
 
-int cd_leiden(const cd_csr*, const cd_params*, uint32_t*, double*) { return CD_ENOTIMPL; }
+int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    CD_TRY(check_driver_params(p));
+    if (p->one_scan) return CD_EINVAL;
+    if (!labels_out) return CD_EINVAL;
+    if (resolve_colors(p) < 2) return CD_EINVAL;  // refinement needs two colour classes or more
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule sched;
+    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level in;
+    CD_TRY(input_level(g, sc, &in));
+    uint32_t *top, *result;
+    CD_TRY(sc.get(&top, in.n));
+    CD_TRY(sc.get(&result, in.n));
+    CD_CUDA(launch_iota(top, in.n, s));
+    CD_CUDA(launch_iota(result, in.n, s));
+    Level cur = in;
+    const uint32_t* init = nullptr;
+    double tol = p->tolerance;
+    int64_t ncom = in.n;
+    for (int pass = 0; pass < p->max_passes && cur.n > 0; ++pass) {
+        uint32_t* lab;
+        int64_t sw = 0;
+        CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, init, &lab, &sw));
+        g_stats.sweeps += sw;
+        g_stats.passes += 1;
+        uint32_t* dc;
+        CD_TRY(sc.get(&dc, cur.n));
+        int64_t nc = 0;
+        CD_TRY(renumber_level(cur, lab, dc, sc, dglob, &nc, s));
+        // result = community (bound) of every input vertex at this level
+        CD_CUDA(cudaMemcpyAsync(result, top, sizeof(uint32_t) * in.n, cudaMemcpyDeviceToDevice, s));
+        CD_CUDA(launch_compose(result, in.n, dc, s));
+        ncom = nc;
+        if (nc == cur.n || pass + 1 >= p->max_passes) break;
+        Level rl = cur;
+        uint32_t* rlab;
+        CD_TRY(refine_level(rl, p, dc, sched, sc, dglob, s, &rlab));
+        uint32_t* dr;
+        CD_TRY(sc.get(&dr, cur.n));
+        int64_t nr = 0;
+        CD_TRY(renumber_level(cur, rlab, dr, sc, dglob, &nr, s));
+        if (nr == cur.n || (double)nr > p->aggregation_tolerance * (double)cur.n) break;
+        // next level: one vertex per sub-community, starting in its bound
+        uint32_t* next_init;
+        CD_TRY(sc.get(&next_init, nr));
+        CD_CUDA(launch_scatter_bound(dr, dc, cur.n, next_init, s));
+        CD_CUDA(launch_compose(top, in.n, dr, s));
+        Level next;
+        CD_TRY(aggregate_level(cur, dr, nr, sc, dglob, s, nullptr, nullptr, nullptr, &next));
+        cur = next;
+        init = next_init;
+        tol /= p->tolerance_drop;
+    }
+    g_stats.communities = ncom;
+    double q = 0.0;
+    CD_TRY(modularity_of(in, result, sc, dglob, s, &q));
+    CD_TRY(emit_labels(g, result, labels_out, s));
+    if (q_out) *q_out = q;
+    return CD_OK;
+}
 
 int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t* dense_out,
                  int64_t* offsets_out, int32_t* cols_out, uint32_t* weights_out, int64_t* n_out,

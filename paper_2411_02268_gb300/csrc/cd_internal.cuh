@@ -58,8 +58,32 @@ struct SweepArgs {
     int64_t nnz;
     int mode;
     int uncond;
+    int one_scan;             // LPA: decide on sketch values, no second scan
+    int colors;               // refine: colour classes of the driver
+    int sub_color;            // refine: colour class deciding in this sub-sweep
     BucketTable bt;
 };
+
+// Colour class of vertex v among `colors` classes: the 32-bit integer hash
+// "lowbias32" (C. Wellons) of v, modulo the number of classes.
+__host__ __device__ __forceinline__ uint32_t color_of(uint32_t v, int colors) {
+    if (colors <= 1) return 0u;
+    uint32_t x = v;
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x % (uint32_t)colors;
+}
+
+// Refine mode (Leiden): a singleton community whose vertex has the colour of
+// the deciding sub-sweep is not a candidate (its only member may leave in the
+// same sub-sweep).  Louvain: a singleton may not join a larger-id singleton.
+__device__ __forceinline__ bool barred(const SweepArgs& a, uint32_t c, uint32_t d, bool d_single) {
+    if (a.mode == CD_MODE_REFINE) return a.size[c] == 1 && (int)color_of(c, a.colors) == a.sub_color;
+    return d_single && c > d && a.size[c] == 1;
+}
 
 // Host-side launchers (sweep.cu).
 cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,
@@ -112,6 +136,8 @@ cudaError_t launch_renumber(const uint32_t* labels, int64_t n, uint32_t* dense, 
                             cudaStream_t s);
 cudaError_t launch_compose(uint32_t* top, int64_t n0, const uint32_t* dense, cudaStream_t s);
 cudaError_t launch_iota(uint32_t* x, int64_t n, cudaStream_t s);
+cudaError_t launch_scatter_bound(const uint32_t* sub, const uint32_t* bound, int64_t n, uint32_t* next_init,
+                                 cudaStream_t s);
 int64_t radix_tiles(int64_t n);
 struct AggScratch {
     uint32_t *src, *dst, *w, *src2, *dst2, *w2, *hist, *heads;

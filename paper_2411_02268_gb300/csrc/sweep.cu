@@ -113,19 +113,6 @@ __device__ __forceinline__ int bucket_of(int64_t deg, const BucketTable& bt) {
     return bt.nb - 1;
 }
 
-// Colour class of vertex i among `colors` classes: the 32-bit integer hash
-// "lowbias32" (C. Wellons) of i, modulo the number of classes.
-__device__ __forceinline__ uint32_t color_of(uint32_t i, int colors) {
-    if (colors <= 1) return 0u;
-    uint32_t x = i;
-    x ^= x >> 16;
-    x *= 0x7feb352dU;
-    x ^= x >> 15;
-    x *= 0x846ca68bU;
-    x ^= x >> 16;
-    return x % (uint32_t)colors;
-}
-
 __device__ __forceinline__ int key_of(const int64_t* __restrict__ off, int64_t v, int64_t n, int64_t nnz,
                                       const BucketTable& bt, int colors, Globals* glob) {
     int64_t o0 = off[v], o1 = off[v + 1];

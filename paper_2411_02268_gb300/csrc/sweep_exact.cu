@@ -94,7 +94,7 @@ __device__ __forceinline__ Best scan_table(const SweepArgs& a, const uint32_t* k
             if (kic <= kid) continue;
             cur.gain = (i128)kic;
         } else {
-            if (sd1 && c > d && a.size[c] == 1) continue;
+            if (barred(a, c, d, sd1)) continue;
             i128 g = (i128)two_m * ((i128)kic - (i128)kid) - (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
             if (g <= 0) continue;
             cur.gain = g;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_group(const SweepArgs a,
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
     const int64_t vi = a.bt.vbegin[bucket] + ((int64_t)blockIdx.x * groups + gi);
     const bool valid = vi < a.bt.vbegin[bucket + 1];
-    uint32_t i = 0, d = 0;
+    uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
     if (valid) {
@@ -163,6 +163,10 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_group(const SweepArgs a,
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.bound) {
+            bi = a.bound[i];
+            if (a.size[d] != 1) act = false;  // refine: only singletons move
+        }
     }
     for (uint32_t s = lane; s < T; s += G) { keys[s] = kEmpty; vals[s] = 0; }
     __syncwarp(gmask);
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_group(const SweepArgs a,
             uint32_t j = (uint32_t)a.cols[e];
             if (j >= (uint32_t)a.n) { atomicOr(&a.glob->err, kErrBadCol); continue; }
             if (j == i) continue;
+            if (a.bound && __ldg(a.bound + j) != bi) continue;
             table_add(keys, vals, T, __ldg(a.labels + j), a.w[e]);
         }
     }
@@ -207,7 +212,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_block(const SweepArgs a,
     const uint32_t i = a.verts[vi];
     const int64_t start = a.off[i], end = a.off[i + 1];
     const uint32_t d = a.labels[i];
-    const bool act = !(a.active && !a.active[i]);
+    const uint32_t bi = a.bound ? a.bound[i] : 0u;
+    const bool act = !(a.active && !a.active[i]) && !(a.bound && a.size[d] != 1);
     uint32_t T;
     uint32_t* keys;
     unsigned long long* vals;
@@ -228,6 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_block(const SweepArgs a,
             uint32_t j = (uint32_t)a.cols[e];
             if (j >= (uint32_t)a.n) { atomicOr(&a.glob->err, kErrBadCol); continue; }
             if (j == i) continue;
+            if (a.bound && __ldg(a.bound + j) != bi) continue;
             table_add(keys, vals, T, __ldg(a.labels + j), a.w[e]);
         }
     }

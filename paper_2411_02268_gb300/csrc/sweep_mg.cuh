@@ -13,36 +13,60 @@ namespace cdk {
 
 // ---------------------------------------------------------------------------
 // Algorithm 1 on a register-resident sketch of K slots.
+//
+// The slot values are kept as t[p] against a per-sketch subtraction total D:
+// the value of slot p is max(t[p] - D, 0).  Subtracting w from every slot
+// (clamped at 0) is then D += w, because clamped subtractions compose
+// (max(max(v - a, 0) - b, 0) = max(v - a - b, 0)); adding w to slot p is
+// t[p] = max(t[p], D) + w; slot p is empty iff t[p] <= D; inserting sets
+// t[p] = D + w.  The values (and so every result) are exactly those of
+// Algorithm 1.  t and D never exceed the row's weighted degree.
+// `lossy` records whether anything was ever subtracted: a sketch that never
+// subtracted holds every community it saw with its exact weight.
 // ---------------------------------------------------------------------------
 template <int K, typename VT>
-__device__ __forceinline__ void mg_update(uint32_t (&key)[K], VT (&val)[K], uint32_t c, VT w,
-                                          bool uncond) {
-    bool has = false;
+struct Sketch {
+    uint32_t key[K];
+    VT t[K];
+    VT D;
+    bool lossy;
+
+    __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int p = 0; p < K; ++p) {
-        bool m = key[p] == c;
-        val[p] += m ? w : (VT)0;
-        has |= m;
+        for (int p = 0; p < K; ++p) { key[p] = kEmpty; t[p] = 0; }
+        D = 0;
+        lossy = false;
     }
-    if (!has) {
-        if (uncond) {
+
+    __device__ __forceinline__ VT value(int p) const { return t[p] > D ? t[p] - D : (VT)0; }
+
+    __device__ __forceinline__ void update(uint32_t c, VT w, bool uncond) {
+        bool has = false;
 #pragma unroll
-            for (int p = 0; p < K; ++p) val[p] = val[p] > w ? val[p] - w : (VT)0;
+        for (int p = 0; p < K; ++p) {
+            const bool m = key[p] == c;
+            const VT up = (t[p] > D ? t[p] : D) + w;
+            t[p] = m ? up : t[p];
+            has |= m;
         }
-        int e = -1;
-#pragma unroll
-        for (int p = 0; p < K; ++p)
-            if (val[p] == 0) e = p;
-        if (e >= 0) {
+        if (!has) {
+            if (uncond) { D += w; lossy = true; }
+            int e = -1;
 #pragma unroll
             for (int p = 0; p < K; ++p)
-                if (p == e) { key[p] = c; val[p] = w; }
-        } else if (!uncond) {
+                if (t[p] <= D) e = p;
+            if (e >= 0) {
+                const VT nt = D + w;
 #pragma unroll
-            for (int p = 0; p < K; ++p) val[p] = val[p] > w ? val[p] - w : (VT)0;
+                for (int p = 0; p < K; ++p)
+                    if (p == e) { key[p] = c; t[p] = nt; }
+            } else if (!uncond) {
+                D += w;
+                lossy = true;
+            }
         }
     }
-}
+};
 
 // Per-vertex decision (Eq. 2 / LPA rule); acc[p] = K_{i->cand[p]}, kid = K_{i->d}.
 template <int K, typename VT>
@@ -71,7 +95,7 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
         for (int p = 0; p < K; ++p) {
             uint32_t c = cand[p];
             if (c == kEmpty) continue;
-            if (sd1 && c > d && a.size[c] == 1) continue;
+            if (barred(a, c, d, sd1)) continue;
             i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
                      (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
             if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; }
@@ -82,41 +106,85 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
     return have;
 }
 
-// Loads chunk ch (4 entries, 16-byte aligned) of the row [start, end) and calls
-// f(col, w) for entries inside the row that are not self-loops.
-template <typename F>
-__device__ __forceinline__ void for_chunk(const SweepArgs& a, int64_t ch, int64_t start, int64_t end,
-                                          uint32_t i, F&& f) {
-    int64_t e0 = ch * 4;
-    int cs[4];
-    uint32_t ws[4];
+// Chunk ch of the CSR: 4 entries, 16-byte aligned.
+struct Chunk {
+    int c[4];
+    uint32_t w[4];
+};
+
+__device__ __forceinline__ Chunk load_chunk(const SweepArgs& a, int64_t ch) {
+    Chunk k;
+    const int64_t e0 = ch * 4;
     if (e0 + 4 <= a.nnz) {
-        int4 cv = __ldg(reinterpret_cast<const int4*>(a.cols) + ch);
-        uint4 wv = __ldg(reinterpret_cast<const uint4*>(a.w) + ch);
-        cs[0] = cv.x; cs[1] = cv.y; cs[2] = cv.z; cs[3] = cv.w;
-        ws[0] = wv.x; ws[1] = wv.y; ws[2] = wv.z; ws[3] = wv.w;
+        const int4 cv = __ldg(reinterpret_cast<const int4*>(a.cols) + ch);
+        const uint4 wv = __ldg(reinterpret_cast<const uint4*>(a.w) + ch);
+        k.c[0] = cv.x; k.c[1] = cv.y; k.c[2] = cv.z; k.c[3] = cv.w;
+        k.w[0] = wv.x; k.w[1] = wv.y; k.w[2] = wv.z; k.w[3] = wv.w;
     } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            bool ok = e0 + u < a.nnz;
-            cs[u] = ok ? a.cols[e0 + u] : -1;
-            ws[u] = ok ? a.w[e0 + u] : 0u;
+            const bool ok = e0 + u < a.nnz;
+            k.c[u] = ok ? a.cols[e0 + u] : -1;
+            k.w[u] = ok ? a.w[e0 + u] : 0u;
         }
     }
-    uint32_t labs[4];
-    bool ok[4];
+    return k;
+}
+
+// Scans the chunks first, first + step, ... < c1 of the row [start, end) and
+// calls f(label of col, w) for entries inside the row that are not self-loops
+// (in refine mode only for neighbours inside the vertex's bound).  The next
+// chunk's loads are issued before the current chunk is processed.
+template <typename F>
+__device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, int64_t c1, int step,
+                                            int64_t start, int64_t end, uint32_t i, uint32_t bi, F&& f) {
+    if (first >= c1) return;
+    Chunk cur = load_chunk(a, first);
+    for (int64_t ch = first; ch < c1; ch += step) {
+        Chunk nxt;
+        const bool more = ch + step < c1;
+        if (more) nxt = load_chunk(a, ch + step);
+        const int64_t e0 = ch * 4;
+        uint32_t labs[4];
+        bool ok[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        int64_t e = e0 + u;
-        const bool in_row = e >= start && e < end;
-        const bool in_range = (uint32_t)cs[u] < (uint32_t)a.n;
-        if (in_row && !in_range) atomicOr(&a.glob->err, kErrBadCol);
-        ok[u] = in_row && in_range && (uint32_t)cs[u] != i;
-        labs[u] = ok[u] ? __ldg(a.labels + cs[u]) : kEmpty;
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = e0 + u;
+            const bool in_row = e >= start && e < end;
+            const bool in_range = (uint32_t)cur.c[u] < (uint32_t)a.n;
+            if (in_row && !in_range) atomicOr(&a.glob->err, kErrBadCol);
+            ok[u] = in_row && in_range && (uint32_t)cur.c[u] != i;
+            labs[u] = ok[u] ? __ldg(a.labels + cur.c[u]) : kEmpty;
+        }
+        if (a.bound) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (ok[u]) ok[u] = __ldg(a.bound + cur.c[u]) == bi;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (ok[u]) f(labs[u], cur.w[u]);
+        if (more) cur = nxt;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (ok[u]) f(labs[u], ws[u]);
+}
+
+// Entry-by-entry scan of a row on one thread (single-stream rows are short:
+// no alignment waste at the row's ends).
+template <typename F>
+__device__ __forceinline__ void for_row(const SweepArgs& a, int64_t start, int64_t end, uint32_t i, uint32_t bi,
+                                        F&& f) {
+#pragma unroll 4
+    for (int64_t e = start; e < end; ++e) {
+        const uint32_t j = (uint32_t)__ldg(a.cols + e);
+        const uint32_t w = __ldg(a.w + e);
+        if (j >= (uint32_t)a.n) {
+            atomicOr(&a.glob->err, kErrBadCol);
+            continue;
+        }
+        if (j == i) continue;
+        if (a.bound && __ldg(a.bound + j) != bi) continue;
+        f(__ldg(a.labels + j), w);
+    }
 }
 
 // Per-thread statistics handed to the block epilogue.
@@ -125,6 +193,16 @@ struct Outcome {
     u128 gain;
     uint32_t vertex;
 };
+
+// Feeds the live slots of a partner sketch (keys pk, values pv) to s.
+template <int K, typename VT>
+__device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk)[K], const VT (&pv)[K],
+                                           bool plossy, bool unc) {
+#pragma unroll
+    for (int p = 0; p < K; ++p)
+        if (pv[p] > 0) s.update(pk[p], pv[p], unc);
+    s.lossy |= plossy;
+}
 
 // ---------------------------------------------------------------------------
 // G streams per vertex inside one warp (G = 1, 2, ..., 32).
@@ -135,7 +213,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     const unsigned gmask = (G == 32) ? 0xffffffffu
                                      : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
     Outcome out{false, 0, 0};
-    uint32_t i = 0, d = 0;
+    uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
     if (valid) {
@@ -144,55 +222,75 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.bound) {
+            bi = a.bound[i];
+            if (a.size[d] != 1) act = false;  // refine: only singletons move
+        }
     }
-    uint32_t key[K];
-    VT val[K];
-#pragma unroll
-    for (int p = 0; p < K; ++p) { key[p] = kEmpty; val[p] = 0; }
+    Sketch<K, VT> sk;
+    sk.init();
     const bool unc = a.uncond != 0;
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
     if (act) {
-        for (int64_t ch = first; ch < c1; ch += G)
-            for_chunk(a, ch, start, end, i, [&](uint32_t c, uint32_t w) {
-                mg_update<K, VT>(key, val, c, (VT)w, unc);
-            });
+        if (G == 1) {
+            for_row(a, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+        } else {
+            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+        }
     }
     // merge tree: S[s] <- merge(S[s], S[s+o]), o = G/2 .. 1
 #pragma unroll 1
     for (int o = G / 2; o >= 1; o >>= 1) {
+        uint32_t pk[K];
+        VT pv[K];
 #pragma unroll
         for (int p = 0; p < K; ++p) {
-            uint32_t ok = __shfl_down_sync(gmask, key[p], o, G);
-            VT ov = __shfl_down_sync(gmask, val[p], o, G);
-            if (lane < o && ov > 0) mg_update<K, VT>(key, val, ok, ov, unc);
+            pk[p] = __shfl_down_sync(gmask, sk.key[p], o, G);
+            pv[p] = __shfl_down_sync(gmask, sk.value(p), o, G);
         }
+        const bool pl = __shfl_down_sync(gmask, (int)sk.lossy, o, G) != 0;
+        if (lane < o) merge_into(sk, pk, pv, pl, unc);
     }
+    // candidates (and, if the sketch never subtracted, their exact weights)
     uint32_t cand[K];
-#pragma unroll
-    for (int p = 0; p < K; ++p) {
-        uint32_t kk = val[p] > 0 ? key[p] : kEmpty;
-        kk = __shfl_sync(gmask, kk, 0, G);
-        cand[p] = kk == d ? kEmpty : kk;
-    }
-    // second scan: exact K_{i->c} for the candidates and for d
     VT acc[K];
     VT kid = 0;
+    // no second scan when the sketch never subtracted (its values are then the
+    // exact linking weights) or in the LPA 1-scan variant (Section 4.3)
+    const bool exact = __shfl_sync(gmask, (int)sk.lossy, 0, G) == 0 || a.one_scan;
 #pragma unroll
-    for (int p = 0; p < K; ++p) acc[p] = 0;
-    if (act) {
-        for (int64_t ch = first; ch < c1; ch += G)
-            for_chunk(a, ch, start, end, i, [&](uint32_t c, uint32_t w) {
+    for (int p = 0; p < K; ++p) {
+        const VT v = sk.value(p);
+        uint32_t kk = v > 0 ? sk.key[p] : kEmpty;
+        kk = __shfl_sync(gmask, kk, 0, G);
+        cand[p] = kk == d ? kEmpty : kk;
+        acc[p] = kk == d ? (VT)0 : v;  // lane 0: exact when the sketch never subtracted
+        kid += kk == d ? v : (VT)0;
+    }
+    if (!exact) {
+        // second scan: exact K_{i->c} for the candidates and for d
+#pragma unroll
+        for (int p = 0; p < K; ++p) acc[p] = 0;
+        kid = 0;
+        if (act) {
+            auto add = [&](uint32_t c, uint32_t w) {
                 kid += c == d ? (VT)w : (VT)0;
 #pragma unroll
                 for (int p = 0; p < K; ++p) acc[p] += c == cand[p] ? (VT)w : (VT)0;
-            });
-    }
+            };
+            if (G == 1) {
+                for_row(a, start, end, i, bi, add);
+            } else {
+                scan_chunks(a, first, c1, G, start, end, i, bi, add);
+            }
+        }
 #pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        kid += __shfl_down_sync(gmask, kid, o, G);
+        for (int o = G / 2; o >= 1; o >>= 1) {
+            kid += __shfl_down_sync(gmask, kid, o, G);
 #pragma unroll
-        for (int p = 0; p < K; ++p) acc[p] += __shfl_down_sync(gmask, acc[p], o, G);
+            for (int p = 0; p < K; ++p) acc[p] += __shfl_down_sync(gmask, acc[p], o, G);
+        }
     }
     if (act && lane == 0) {
         uint32_t best;
@@ -216,8 +314,11 @@ template <int K, typename VT>
 struct BlockSmem {
     uint32_t k[128][K];
     VT v[128][K];
+    int lossy[128];
     VT acc[8][K + 1];
     uint32_t cand[4][K];
+    VT cval[4][K];
+    int exact[4];
 };
 
 __device__ __forceinline__ void sub_barrier(int id, int nthreads) {
@@ -234,7 +335,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     const int wl = s >> 5;          // warp within sub-block
     const int lane = s & 31;
     Outcome out{false, 0, 0};
-    uint32_t i = 0, d = 0;
+    uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
     if (valid) {
@@ -243,19 +344,18 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.bound) {
+            bi = a.bound[i];
+            if (a.size[d] != 1) act = false;  // refine: only singletons move
+        }
     }
-    uint32_t key[K];
-    VT val[K];
-#pragma unroll
-    for (int p = 0; p < K; ++p) { key[p] = kEmpty; val[p] = 0; }
+    Sketch<K, VT> sk;
+    sk.init();
     const bool unc = a.uncond != 0;
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((s - (int)(c0 & (L - 1))) & (L - 1));
     if (act) {
-        for (int64_t ch = first; ch < c1; ch += L)
-            for_chunk(a, ch, start, end, i, [&](uint32_t c, uint32_t w) {
-                mg_update<K, VT>(key, val, c, (VT)w, unc);
-            });
+        scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
     }
     // cross-warp rounds through shared memory (o = L/2 .. 32)
     const int slot_base = sb * (L / 2);  // (256/L) sub-blocks x L/2 slots = 128
@@ -264,17 +364,21 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
         if (s >= o && s < 2 * o) {
 #pragma unroll
             for (int p = 0; p < K; ++p) {
-                sm.k[slot_base + s - o][p] = key[p];
-                sm.v[slot_base + s - o][p] = val[p];
+                sm.k[slot_base + s - o][p] = sk.key[p];
+                sm.v[slot_base + s - o][p] = sk.value(p);
             }
+            sm.lossy[slot_base + s - o] = (int)sk.lossy;
         }
         sub_barrier(bar, L);
         if (s < o) {
+            uint32_t pk[K];
+            VT pv[K];
 #pragma unroll
             for (int p = 0; p < K; ++p) {
-                VT ov = sm.v[slot_base + s][p];
-                if (ov > 0) mg_update<K, VT>(key, val, sm.k[slot_base + s][p], ov, unc);
+                pk[p] = sm.k[slot_base + s][p];
+                pv[p] = sm.v[slot_base + s][p];
             }
+            merge_into(sk, pk, pv, sm.lossy[slot_base + s] != 0, unc);
         }
         sub_barrier(bar, L);
     }
@@ -282,56 +386,72 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     if (wl == 0) {
 #pragma unroll 1
         for (int o = 16; o >= 1; o >>= 1) {
+            uint32_t pk[K];
+            VT pv[K];
 #pragma unroll
             for (int p = 0; p < K; ++p) {
-                uint32_t ok = __shfl_down_sync(0xffffffffu, key[p], o);
-                VT ov = __shfl_down_sync(0xffffffffu, val[p], o);
-                if (lane < o && ov > 0) mg_update<K, VT>(key, val, ok, ov, unc);
+                pk[p] = __shfl_down_sync(0xffffffffu, sk.key[p], o);
+                pv[p] = __shfl_down_sync(0xffffffffu, sk.value(p), o);
             }
+            const bool pl = __shfl_down_sync(0xffffffffu, (int)sk.lossy, o) != 0;
+            if (lane < o) merge_into(sk, pk, pv, pl, unc);
         }
         if (lane == 0) {
 #pragma unroll
             for (int p = 0; p < K; ++p) {
-                uint32_t kk = val[p] > 0 ? key[p] : kEmpty;
-                sm.cand[sb][p] = kk == d ? kEmpty : kk;
+                const VT v = sk.value(p);
+                sm.cand[sb][p] = v > 0 ? sk.key[p] : kEmpty;
+                sm.cval[sb][p] = v;
             }
+            sm.exact[sb] = sk.lossy ? 0 : 1;
         }
     }
     sub_barrier(bar, L);
     uint32_t cand[K];
-#pragma unroll
-    for (int p = 0; p < K; ++p) cand[p] = sm.cand[sb][p];
     VT acc[K];
     VT kid = 0;
 #pragma unroll
-    for (int p = 0; p < K; ++p) acc[p] = 0;
-    if (act) {
-        for (int64_t ch = first; ch < c1; ch += L)
-            for_chunk(a, ch, start, end, i, [&](uint32_t c, uint32_t w) {
+    for (int p = 0; p < K; ++p) {
+        const uint32_t kk = sm.cand[sb][p];
+        const VT v = sm.cval[sb][p];
+        cand[p] = kk == d ? kEmpty : kk;
+        acc[p] = kk == d ? (VT)0 : v;
+        kid += kk == d ? v : (VT)0;
+    }
+    const bool exact = sm.exact[sb] != 0 || a.one_scan;
+    if (!exact) {
+#pragma unroll
+        for (int p = 0; p < K; ++p) acc[p] = 0;
+        kid = 0;
+        if (act) {
+            scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) {
                 kid += c == d ? (VT)w : (VT)0;
 #pragma unroll
                 for (int p = 0; p < K; ++p) acc[p] += c == cand[p] ? (VT)w : (VT)0;
             });
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        kid += __shfl_down_sync(0xffffffffu, kid, o);
-#pragma unroll
-        for (int p = 0; p < K; ++p) acc[p] += __shfl_down_sync(0xffffffffu, acc[p], o);
-    }
-    const int wbase = sb * W;  // this sub-block's rows of sm.acc
-    if (lane == 0) {
-#pragma unroll
-        for (int p = 0; p < K; ++p) sm.acc[wbase + wl][p] = acc[p];
-        sm.acc[wbase + wl][K] = kid;
-    }
-    sub_barrier(bar, L);
-    if (s == 0) {
-        for (int q = 1; q < W; ++q) {
-#pragma unroll
-            for (int p = 0; p < K; ++p) acc[p] += sm.acc[wbase + q][p];
-            kid += sm.acc[wbase + q][K];
         }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            kid += __shfl_down_sync(0xffffffffu, kid, o);
+#pragma unroll
+            for (int p = 0; p < K; ++p) acc[p] += __shfl_down_sync(0xffffffffu, acc[p], o);
+        }
+        const int wbase = sb * W;  // this sub-block's rows of sm.acc
+        if (lane == 0) {
+#pragma unroll
+            for (int p = 0; p < K; ++p) sm.acc[wbase + wl][p] = acc[p];
+            sm.acc[wbase + wl][K] = kid;
+        }
+        sub_barrier(bar, L);
+        if (s == 0) {
+            for (int q = 1; q < W; ++q) {
+#pragma unroll
+                for (int p = 0; p < K; ++p) acc[p] += sm.acc[wbase + q][p];
+                kid += sm.acc[wbase + q][K];
+            }
+        }
+    }
+    if (s == 0) {
         if (act) {
             uint32_t best;
             u128 g;
@@ -344,7 +464,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
             a.labels_out[i] = d;
         }
     }
-    sub_barrier(bar, L);  // sm is reused by nothing after this, but keep phases clean
+    sub_barrier(bar, L);
     return out;
 }
 
@@ -375,14 +495,17 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const Outcome& o) {
 }
 
 template <int K, typename VT>
-__global__ void __launch_bounds__(kBlock) k_sweep_mg(const SweepArgs a) {
+__global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) k_sweep_mg(const SweepArgs a) {
     __shared__ BlockSmem<K, VT> sm;
+    // blocks of the longest rows first, so that they start at once and
+    // overlap with the many short rows instead of trailing the launch
+    const int64_t blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
     int b = 0;
 #pragma unroll
     for (int q = 1; q < CD_MAX_BUCKETS; ++q)
-        if (q < a.bt.nb && (int64_t)blockIdx.x >= a.bt.bbegin[q]) b = q;
+        if (q < a.bt.nb && blk >= a.bt.bbegin[q]) b = q;
     const int L = a.bt.lanes[b];
-    const int64_t lb = (int64_t)blockIdx.x - a.bt.bbegin[b];
+    const int64_t lb = blk - a.bt.bbegin[b];
     const int vpb = L >= kBlock ? 1 : kBlock / L;
     const int64_t vi = a.bt.vbegin[b] + lb * vpb + threadIdx.x / L;
     const bool valid = vi < a.bt.vbegin[b + 1];

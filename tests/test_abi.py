@@ -47,7 +47,7 @@ def test_struct_layout_matches_header(cd, tmp_path):
 int main(void) {
   printf("csr %zu %zu %zu\n", sizeof(cd_csr), offsetof(cd_csr, weights), offsetof(cd_csr, memory));
   printf("sched %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes));
-  printf("params %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors));
+  printf("params %zu %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors), offsetof(cd_params, one_scan));
   printf("stats %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, cuda_error));
   printf("parts %zu\n", sizeof(cd_modularity_parts));
   return 0;
@@ -59,7 +59,7 @@ int main(void) {
     exp = [
         f"csr {C.sizeof(cd.CSR)} {cd.CSR.weights.offset} {cd.CSR.memory.offset}",
         f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset}",
-        f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset}",
+        f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset} {cd.Params.one_scan.offset}",
         f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.cuda_error.offset}",
         f"parts {C.sizeof(cd.ModularityParts)}",
     ]
@@ -95,6 +95,9 @@ def test_argument_checks_without_gpu(cd):
     assert rc(cd.make_params(k=8, subtract=2)) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8), mode=7) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8), lo=lab) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=8, one_scan=True), mode=cd.MODE_LOUVAIN) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=0, one_scan=True), mode=cd.MODE_LPA) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=8), mode=cd.MODE_REFINE) == cd.CD_EINVAL   # refine needs a bound
     bad_sched = cd.schedule_from([4, 2], [1, 2])
     assert rc(cd.make_params(k=8, schedule=bad_sched)) == cd.CD_EINVAL
     bad_sched = cd.schedule_from([4, 10**9], [1, 3])

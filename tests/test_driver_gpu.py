@@ -134,3 +134,35 @@ def test_degenerate_driver_inputs(env):
     assert lab.cpu().numpy().tolist() == [0, 1, 2, 3]
     with pytest.raises(cd.CDError):
         cd.cd_louvain(cd.Graph.to_device(empty), cd.make_params(k=8, tolerance_drop=0.5))
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k", [8, 0, 16])
+def test_leiden_bit_exact_with_twin(env, gname, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    G = cd.Graph.to_device(g)
+    lab, q = cd.cd_leiden(G, cd.make_params(k=k))
+    got = lab.cpu().numpy().view(np.uint32)
+    ref = oracle.leiden_sync(g, k=k, sched=sched_of(cd, k), threads=8)
+    assert np.array_equal(got, ref)
+    assert q == pytest.approx(float(oracle.modularity_fraction(g, ref)), abs=1e-15)
+
+
+def test_leiden_rejects_single_colour(env):
+    cd, torch = env
+    g = GRAPHS["sbm10k"]()
+    with pytest.raises(cd.CDError) as ei:
+        cd.cd_leiden(cd.Graph.to_device(g), cd.make_params(k=8, colors=1))
+    assert ei.value.code == cd.CD_EINVAL
+
+
+@pytest.mark.parametrize("gname", ["sbm10k", "rmat13"])
+def test_lpa_one_scan_bit_exact_with_twin(env, gname):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    lab, q = cd.cd_lpa(cd.Graph.to_device(g), cd.make_params(k=8, tolerance=0.05, one_scan=True))
+    ref = oracle.lpa_sync(g, k=8, sched=sched_of(cd, 8), threads=8, one_scan=True)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)
+    with pytest.raises(cd.CDError):
+        cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=8, one_scan=True))

@@ -437,3 +437,59 @@ def test_sync_louvain_below_brute_force():
         for colors in (1, 8):
             lab = oracle.louvain_sync(g, k=8, colors=colors, tol=0.0)
             assert oracle.modularity_fraction(g, lab) <= qstar
+
+
+def _components_ok(g, lab):
+    """Every label class induces a connected subgraph (BFS)."""
+    from collections import deque
+    for c in np.unique(lab):
+        mem = np.nonzero(lab == c)[0]
+        ms = set(mem.tolist())
+        seen = {int(mem[0])}
+        q = deque([int(mem[0])])
+        while q:
+            u = q.popleft()
+            for e in range(g.offsets[u], g.offsets[u + 1]):
+                v = int(g.cols[e])
+                if v in ms and v not in seen:
+                    seen.add(v)
+                    q.append(v)
+        if len(seen) != len(mem):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("k", [0, 8])
+def test_refinement_nested_and_connected(seed, k):
+    """Leiden refinement (Section 3.4): every refined sub-community lies inside
+    one community of the bound and is connected (Section 5.1.4: no internally
+    disconnected communities); only singletons moved."""
+    g = gen.sbm(400, 8, 0.08, 0.01, wmax=6, seed=seed)
+    bound = oracle.louvain_sync(g, k=k, max_passes=1, threads=2)
+    ref = oracle.refine_sync(g, bound, k=k, threads=2)
+    for c in np.unique(ref):
+        assert len(np.unique(bound[ref == c])) == 1
+    assert _components_ok(g, ref)
+    # refinement merges something on a community-rich graph
+    assert len(np.unique(ref)) < g.n
+
+
+def test_refinement_needs_two_colours():
+    """With one colour class every singleton target is barred: nothing moves."""
+    g = gen.sbm(200, 4, 0.2, 0.01, seed=3)
+    bound = oracle.louvain_sync(g, k=8, max_passes=1)
+    ref = oracle.refine_sync(g, bound, k=8, colors=1)
+    assert np.array_equal(ref, np.arange(g.n))
+
+
+def test_leiden_quality_and_bounds():
+    g = gen.sbm_10k(1)
+    q_lei = oracle.modularity(g, oracle.leiden_sync(g, k=0, threads=4))
+    q_lou = oracle.modularity(g, oracle.louvain_sync(g, k=0, threads=4))
+    assert q_lei >= q_lou - 0.01
+    for seed in range(3):
+        t = gen.random_graph(8, 14, 4, seed=800 + seed)
+        if t.nnz:
+            qstar, _ = oracle.brute_force_best(t)
+            assert oracle.modularity_fraction(t, oracle.leiden_sync(t, k=8, tol=0.0)) <= qstar

@@ -265,3 +265,52 @@ def test_repeatable(env):
     a = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8)
     b = gpu_sweep(cd, torch, g, lab, oracle.MODE_LOUVAIN, 8)
     assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+
+
+@pytest.mark.parametrize("gname", ["sbm10k", "rmat12_w16", "ragged_loops", "grid_rewired"])
+@pytest.mark.parametrize("k", [8, 16, 0])
+def test_refine_sub_sweep_parity(env, gname, k):
+    """One refine-mode sub-sweep (Leiden, Section 3.4): bound filter, the
+    singleton-only rule and the same-colour singleton bar, per colour class,
+    from singletons and from a partly merged state."""
+    cd, torch = env
+    g = GRAPHS[gname]()
+    colors = 8
+    col = oracle.color_classes(g.n, colors)
+    bound = oracle.louvain_sync(g, k=8, max_passes=1, threads=4)
+    sched = cd.cd_default_schedule(k)
+    osched = oracle_sched(cd, sched)
+    states = [np.arange(g.n, dtype=np.uint32),
+              oracle.sweep(g, np.arange(g.n, dtype=np.uint32), oracle.MODE_REFINE, 8, False, osched,
+                           active=(col == 0).astype(np.uint8), bound=bound, colors=colors, sub_color=0)[0]]
+    for lab in states:
+        for p in (0, 3, 7):
+            act = (col == p).astype(np.uint8)
+            params = cd.make_params(k=k, colors=colors, sub_color=p, stream=torch.cuda.current_stream().cuda_stream)
+            G = cd.Graph.to_device(g)
+            out, moved, gain = cd.cd_sweep(G, params, cd.MODE_REFINE,
+                                           torch.from_numpy(lab.view(np.int32)).cuda(),
+                                           active=torch.from_numpy(act).cuda(),
+                                           bound=torch.from_numpy(bound.view(np.int32)).cuda())
+            ref, gains = oracle.sweep(g, lab, oracle.MODE_REFINE, k, False, osched, active=act, bound=bound,
+                                      threads=4, colors=colors, sub_color=p)
+            got = out.cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, ref)
+            assert moved == int(np.count_nonzero(ref != lab))
+            assert gain == oracle.gain_total(gains)
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k", [1, 8])
+def test_lpa_one_scan_parity(env, gname, k):
+    """LPA 1-scan (Section 4.3): decisions on the sketch values alone."""
+    cd, torch = env
+    g = GRAPHS[gname]()
+    osched = oracle_sched(cd, cd.cd_default_schedule(k))
+    for _, lab in label_states(g, 9):
+        G = cd.Graph.to_device(g)
+        p = cd.make_params(k=k, one_scan=True)
+        out, moved, gain = cd.cd_sweep(G, p, cd.MODE_LPA, torch.from_numpy(lab.view(np.int32)).cuda())
+        ref, gains = oracle.sweep(g, lab, oracle.MODE_LPA, k, False, osched, threads=4, one_scan=True)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
+        assert gain == oracle.gain_total(gains)
