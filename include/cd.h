@@ -113,6 +113,9 @@ typedef struct cd_params {
     int32_t one_scan;     /* LPA only (cd_sweep mode LPA, cd_lpa): the "1-scan" variant of
                              Section 4.3, deciding on the sketch values without the second
                              scan (needs k > 0) */
+    int32_t agg_k;        /* drivers: 0 = exact aggregation (sort + segmented sum); 1..16
+                             (power of two) = MG aggregation with agg_k slots (Section 4.1;
+                             Leiden uses its symmetric form, Section 4.2), see cd_aggregate_mg */
 } cd_params;
 
 typedef struct cd_stats {
@@ -204,6 +207,24 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
 int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t* dense_out,
                  int64_t* offsets_out, int32_t* cols_out, uint32_t* weights_out,
                  int64_t* n_out, int64_t* nnz_out);
+
+/* MG aggregation (Section 4.1, "aggregation phase", Fig. 3): like
+ * cd_aggregate, but super-vertex c links only to the communities left in one
+ * k-slot MG sketch (Algorithm 1, subtract as in cd_params) fed with the edges
+ * of all members of c (ascending vertex id, each row in stored order,
+ * self-loops kept), streams and merge tree as in the sweep (schedule by the
+ * community's total entry count; NULL = default), with the sketch values as
+ * weights and no second pass.  symmetric = 0: row c = the live slots of
+ * sketch(c), sorted by column (may be asymmetric, as in the paper's Louvain).
+ * symmetric = 1 (Leiden, Section 4.2): every live slot (c, d, v) yields
+ * (c, d) and (d, c); when sketch(c) holds d and sketch(d) holds c, the value
+ * of the smaller community's sketch is kept.  k: 1, 2, 4, 8 or 16.  Device
+ * memory only; outputs as cd_aggregate (cols_out and weights_out hold nnz
+ * entries, which bounds the result for an undirected input; CD_EINVAL if the
+ * result would not fit); CD_EOVERFLOW if a value exceeds 32 bits. */
+int cd_aggregate_mg(const cd_csr* g, const uint32_t* labels, int k, int subtract, int symmetric,
+                    const cd_schedule* sched, void* stream, uint32_t* dense_out, int64_t* offsets_out,
+                    int32_t* cols_out, uint32_t* weights_out, int64_t* n_out, int64_t* nnz_out);
 
 /*
  * Modularity without any device allocation.  The paper has no counterpart:

@@ -80,6 +80,8 @@ def _load():
             lib.or_local_move_seq.argtypes = [_i64, _p, _p, _p, _p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, ctypes.c_int]
             lib.or_local_move_seq.restype = ctypes.c_int
+            lib.or_aggregate_mg_sketch.argtypes = [_i64, _p, _p, _p, _p, _i64, _p, _p, ctypes.c_int,
+                                                   ctypes.c_int, ctypes.c_int, _p, _p, ctypes.c_int, _p, _p]
             _lib = lib
     return _lib
 
@@ -290,6 +292,62 @@ def aggregate(g, labels):
     return G2, dense
 
 
+def aggregate_mg(g, labels, k: int = 8, uncond: bool = False, sched: Schedule | None = None,
+                 symmetric: bool = False):
+    """MG aggregation (Section 4.1, Fig. 3): super-vertex c links to the live
+    slots of one MG sketch over all edges of c's members (no second pass).
+    symmetric=False (Louvain): row c = the live slots of sketch(c), sorted
+    by key.  symmetric=True (Leiden, Section 4.2: forward and reverse edge
+    both inserted, an edge already present kept): every live slot (c, d, v)
+    yields (c, d) and (d, c); when both sketch(c) holds d and sketch(d)
+    holds c, the value from the smaller community's sketch is kept (the
+    paper's first-inserted edge, with a fixed order).  Returns (G', dense)."""
+    from types import SimpleNamespace
+    sched = sched or Schedule.single_stream()
+    dense, nc = renumber(labels)
+    off, cols, w = _csr(g)
+    order = np.argsort(dense, kind="stable").astype(np.uint32)
+    moff = np.zeros(nc + 1, dtype=np.int64)
+    np.cumsum(np.bincount(dense, minlength=nc), out=moff[1:])
+    keys = np.empty(nc * k, dtype=np.uint32)
+    vals = np.empty(nc * k, dtype=np.uint64)
+    _load().or_aggregate_mg_sketch(g.n, _ptr(off), _ptr(cols), _ptr(w), _ptr(dense), nc, _ptr(moff),
+                                   _ptr(order), k, int(uncond), len(sched.lanes), _ptr(sched.deg_max),
+                                   _ptr(sched.lanes), sched.vec, _ptr(keys), _ptr(vals))
+    src = np.repeat(np.arange(nc, dtype=np.int64), k)
+    live = vals > 0
+    s, d, v = src[live], keys[live].astype(np.int64), vals[live]
+    if symmetric:
+        own = {(int(a), int(b)): int(x) for a, b, x in zip(s, d, v)}
+        edges = {}
+        for (a, b), x in own.items():
+            lo, hi = (a, b) if a <= b else (b, a)
+            if (lo, hi) in edges:
+                continue
+            # value from the smaller community's sketch when it has the pair
+            val = own.get((lo, hi), x) if lo != hi else x
+            edges[(lo, hi)] = val
+        ss, dd, vv = [], [], []
+        for (lo, hi), x in edges.items():
+            ss.append(lo); dd.append(hi); vv.append(x)
+            if lo != hi:
+                ss.append(hi); dd.append(lo); vv.append(x)
+        s = np.array(ss, dtype=np.int64)
+        d = np.array(dd, dtype=np.int64)
+        v = np.array(vv, dtype=np.uint64)
+    key = s * nc + d
+    o = np.argsort(key, kind="stable")
+    s, d, v = s[o], d[o], v[o]
+    counts = np.bincount(s, minlength=nc) if len(s) else np.zeros(nc, dtype=np.int64)
+    noff = np.zeros(nc + 1, dtype=np.int64)
+    np.cumsum(counts, out=noff[1:])
+    if len(v) and int(v.max()) >= 2**32:
+        raise OverflowError("aggregated weight does not fit uint32")
+    G2 = SimpleNamespace(n=nc, offsets=noff, cols=d.astype(np.int32), w=v.astype(np.uint32),
+                         name=getattr(g, "name", "") + "'mg")
+    return G2, dense
+
+
 # ---- whole algorithms ------------------------------------------------------------------
 
 def local_move_seq(g, labels, mode=MODE_LOUVAIN, k=8, uncond=False, tol=0.01, max_sweeps=20):
@@ -417,8 +475,9 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
 
 
 def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
-                 agg_tol=0.8, sched=None, threads=1, colors=8):
-    """Louvain with colour-class sub-sweeps: the exact schedule of cd_louvain."""
+                 agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0):
+    """Louvain with colour-class sub-sweeps: the exact schedule of cd_louvain
+    (agg_k > 0: MG aggregation with agg_k slots)."""
     sched = sched or Schedule.single_stream()
     top = np.arange(g.n, dtype=np.uint32)
     cur = g
@@ -430,7 +489,10 @@ def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, m
         top = dense[top]
         if nc == cur.n or nc > agg_tol * cur.n or p + 1 >= max_passes:
             break
-        cur, _ = aggregate(cur, dense)
+        if agg_k > 0:
+            cur, _ = aggregate_mg(cur, dense, agg_k, uncond, sched)
+        else:
+            cur, _ = aggregate(cur, dense)
         tol /= tol_drop
     return top
 
@@ -464,7 +526,7 @@ def refine_sync(g, bound, k=8, uncond=False, sched=None, threads=1, colors=8):
 
 
 def leiden_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
-                agg_tol=0.8, sched=None, threads=1, colors=8):
+                agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0):
     """Leiden (Section 3.4): local-moving (from the previous level's bounds),
     refinement within the communities found, aggregation by the refined
     partition, repeated; the result is the last level's communities mapped
@@ -488,7 +550,10 @@ def leiden_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, ma
         nxt = np.empty(nr, dtype=np.uint32)
         nxt[dr] = dc
         top = dr[top]
-        cur, _ = aggregate(cur, dr)
+        if agg_k > 0:
+            cur, _ = aggregate_mg(cur, dr, agg_k, uncond, sched, symmetric=True)
+        else:
+            cur, _ = aggregate(cur, dr)
         init = nxt
         tol /= tol_drop
     return renumber(result)[0]

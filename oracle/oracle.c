@@ -407,3 +407,51 @@ int or_local_move_seq(int64_t n, const int64_t* off, const int32_t* cols, const 
     free(K); free(Sig); free(size); free(keys); free(vals);
     return sweeps;
 }
+
+/* ---------------------------------------------------------------------------
+ * MG aggregation (Section 4.1, "aggregation phase", Fig. 3): the super-vertex
+ * of community c keeps the k-majority neighbouring communities of c found by
+ * one MG sketch over the edges of all members of c, with the sketch values
+ * as (approximate) weights and no second pass.  Members are taken in
+ * ascending vertex id, the edges of each in CSR order; self-loops are kept
+ * (the "exclude self" rule is for the local-moving and refinement phases).
+ * The stream partition follows the schedule by the community's total entry
+ * count: entry e (global CSR index) goes to stream (e / V) mod L, streams
+ * merged by the same tree as the sweep.
+ * members: vertex ids grouped by community (ascending within a community),
+ * member_off[nc+1].  keys_out, vals_out: nc * k.
+ * ------------------------------------------------------------------------- */
+void or_aggregate_mg_sketch(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t* w,
+                            const uint32_t* dense, int64_t nc, const int64_t* member_off,
+                            const uint32_t* members, int k, int uncond, int nbuckets,
+                            const int64_t* deg_max, const int32_t* lanes, int vec,
+                            uint32_t* keys_out, uint64_t* vals_out) {
+    or_sched sched = {nbuckets, deg_max, lanes, vec};
+    (void)n;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t total = 0;
+        for (int64_t q = member_off[c]; q < member_off[c + 1]; ++q) {
+            uint32_t i = members[q];
+            total += off[i + 1] - off[i];
+        }
+        int64_t L = streams_for(&sched, total);
+        int64_t V = sched.vec;
+        uint32_t* SK = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(L * k));
+        uint64_t* SV = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(L * k));
+        for (int64_t x = 0; x < L * k; ++x) { SK[x] = EMPTY_KEY; SV[x] = 0; }
+        for (int64_t q = member_off[c]; q < member_off[c + 1]; ++q) {
+            uint32_t i = members[q];
+            for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+                int64_t s = (e / V) % L;
+                or_sketch_update(SK + s * k, SV + s * k, k, dense[cols[e]], w[e], uncond);
+            }
+        }
+        for (int64_t o = L / 2; o >= 1; o /= 2)
+            for (int64_t s = 0; s < o; ++s)
+                or_sketch_merge(SK + s * k, SV + s * k, SK + (s + o) * k, SV + (s + o) * k, k, uncond);
+        memcpy(keys_out + c * k, SK, sizeof(uint32_t) * (size_t)k);
+        memcpy(vals_out + c * k, SV, sizeof(uint64_t) * (size_t)k);
+        free(SK);
+        free(SV);
+    }
+}

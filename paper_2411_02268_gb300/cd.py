@@ -24,7 +24,7 @@ MAX_BUCKETS = 16
 
 # Symbols declared in include/cd.h.
 SYMBOLS = ("cd_strerror", "cd_last_stats", "cd_default_schedule", "cd_sweep", "cd_modularity",
-           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_modularity_noalloc")
+           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_aggregate_mg", "cd_modularity_noalloc")
 
 
 class CSR(ctypes.Structure):
@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("sched", ctypes.POINTER(Schedule)), ("stream", ctypes.c_void_p),
                 ("timing", ctypes.c_int32), ("colors", ctypes.c_int32),
-                ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32)]
+                ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32), ("agg_k", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -99,6 +99,9 @@ def lib():
                                              ctypes.POINTER(ctypes.c_double)]
             L.cd_aggregate.argtypes = [ctypes.POINTER(CSR), P, P, P, P, P, P,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+            L.cd_aggregate_mg.argtypes = [ctypes.POINTER(CSR), P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(Schedule), P, P, P, P, P,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
             for name in SYMBOLS:
                 if name != "cd_strerror":
                     getattr(L, name).restype = ctypes.c_int
@@ -164,7 +167,7 @@ def current_stream():
 
 def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregation_tolerance=0.8,
                 max_sweeps=20, max_passes=10, schedule: Schedule | None = None, stream=None,
-                timing=False, colors=0, sub_color=0, one_scan=False) -> Params:
+                timing=False, colors=0, sub_color=0, one_scan=False, agg_k=0) -> Params:
     p = Params()
     p.k, p.subtract = int(k), int(subtract)
     p.tolerance, p.tolerance_drop, p.aggregation_tolerance = tolerance, tolerance_drop, aggregation_tolerance
@@ -175,6 +178,7 @@ def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregatio
     p.colors = int(colors)
     p.sub_color = int(sub_color)
     p.one_scan = int(bool(one_scan))
+    p.agg_k = int(agg_k)
     p._keep = schedule
     return p
 
@@ -284,5 +288,26 @@ def cd_aggregate(g: Graph, labels, stream=None):
     st = stream.value if isinstance(stream, ctypes.c_void_p) else stream
     _check(lib().cd_aggregate(ctypes.byref(csr), _ptr(labels), st, _ptr(dense), _ptr(off), _ptr(cols), _ptr(w),
                               ctypes.byref(n_out), ctypes.byref(nnz_out)), "cd_aggregate")
+    n2, m2 = n_out.value, nnz_out.value
+    return dense, Graph(n2, off[:n2 + 1], cols[:m2], w[:m2])
+
+
+def cd_aggregate_mg(g: Graph, labels, k=8, subtract=0, symmetric=False, schedule: Schedule | None = None,
+                    stream=None):
+    """MG aggregation; returns (dense labels, super-graph as Graph of device tensors)."""
+    import torch
+    dev = g.offsets.device
+    dense = torch.empty(g.n, dtype=torch.int32, device=dev)
+    off = torch.empty(g.n + 1, dtype=torch.int64, device=dev)
+    cap = max(g.nnz, 1)
+    cols = torch.empty(cap, dtype=torch.int32, device=dev)
+    w = torch.empty(cap, dtype=torch.int32, device=dev)
+    n_out, nnz_out = ctypes.c_int64(), ctypes.c_int64()
+    csr = g.csr()
+    st = stream.value if isinstance(stream, ctypes.c_void_p) else stream
+    sp = ctypes.byref(schedule) if schedule is not None else None
+    _check(lib().cd_aggregate_mg(ctypes.byref(csr), _ptr(labels), k, subtract, int(symmetric), sp, st, _ptr(dense),
+                                 _ptr(off), _ptr(cols), _ptr(w), ctypes.byref(n_out), ctypes.byref(nnz_out)),
+           "cd_aggregate_mg")
     n2, m2 = n_out.value, nnz_out.value
     return dense, Graph(n2, off[:n2 + 1], cols[:m2], w[:m2])

@@ -216,14 +216,15 @@ int bits_for(int64_t nc) {
     return b;
 }
 
-// Sorts (src, dst, w) by (src, dst).  On return the sorted arrays are in
-// (src, dst, w) (the buffers may have been swapped with the *2 ones).
-cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* glob, cudaStream_t s) {
-    int bits = bits_for(nc);
+// Stable LSD sort of (src, dst, w): passes over the low `bits_dst` bits of dst,
+// then the low `bits_src` bits of src, so the result is ordered by (src, dst)
+// with ties in input order.  On return the sorted arrays are in (src, dst, w)
+// (the buffers may have been swapped with the *2 ones).
+cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_dst, Globals* glob, cudaStream_t s) {
     int64_t nt = radix_tiles(nnz);
     int64_t hn = nt * 256;
-    // by dst, then by src: key passes
     for (int which = 0; which < 2; ++which) {
+        const int bits = which == 0 ? bits_dst : bits_src;
         for (int shift = 0; shift < bits; shift += 8) {
             uint32_t* key = which == 0 ? a.dst : a.src;
             uint32_t* p1 = which == 0 ? a.src : a.dst;
@@ -239,6 +240,176 @@ cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* gl
             std::swap(a.w, a.w2);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* glob, cudaStream_t s) {
+    const int b = bits_for(nc);
+    return radix_sort_keys(a, nnz, b, b, glob, s);
+}
+
+// ---- MG aggregation support ---------------------------------------------------------
+
+// cnt[dense[i]] += 1 and ecnt[dense[i]] += deg(i)
+__global__ void k_community_counts(const int64_t* __restrict__ off, const uint32_t* __restrict__ dense, int64_t n,
+                                   uint32_t* __restrict__ cnt, uint32_t* __restrict__ ecnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t c = dense[i];
+    atomicAdd(&cnt[c], 1u);
+    const uint32_t d = (uint32_t)(off[i + 1] - off[i]);
+    if (d) atomicAdd(&ecnt[c], d);
+}
+
+cudaError_t launch_community_counts(const int64_t* off, const uint32_t* dense, int64_t n, uint32_t* cnt,
+                                    uint32_t* ecnt, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_community_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, dense, n, cnt, ecnt);
+    return cudaGetLastError();
+}
+
+// Sketch slots of community c -> live entries sorted by key (in place), count.
+template <int K>
+__device__ void sort_slots(uint32_t* keys, unsigned long long* vals, uint32_t* count) {
+    uint32_t k[K];
+    unsigned long long v[K];
+    int m = 0;
+    for (int p = 0; p < K; ++p) {
+        if (vals[p] > 0) { k[m] = keys[p]; v[m] = vals[p]; ++m; }
+    }
+    for (int x = 1; x < m; ++x) {  // insertion sort (K <= 16)
+        uint32_t kk = k[x];
+        unsigned long long vv = v[x];
+        int y = x - 1;
+        while (y >= 0 && k[y] > kk) { k[y + 1] = k[y]; v[y + 1] = v[y]; --y; }
+        k[y + 1] = kk;
+        v[y + 1] = vv;
+    }
+    for (int p = 0; p < K; ++p) {
+        keys[p] = p < m ? k[p] : kEmpty;
+        vals[p] = p < m ? v[p] : 0ull;
+    }
+    *count = (uint32_t)m;
+}
+
+__global__ void k_mg_sort_rows(uint32_t* __restrict__ keys, unsigned long long* __restrict__ vals, int64_t nc, int k,
+                               uint32_t* __restrict__ count, uint32_t* __restrict__ self_less) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    uint32_t* kk = keys + c * k;
+    unsigned long long* vv = vals + c * k;
+    switch (k) {
+        case 1: sort_slots<1>(kk, vv, &count[c]); break;
+        case 2: sort_slots<2>(kk, vv, &count[c]); break;
+        case 4: sort_slots<4>(kk, vv, &count[c]); break;
+        case 8: sort_slots<8>(kk, vv, &count[c]); break;
+        default: sort_slots<16>(kk, vv, &count[c]); break;
+    }
+    if (self_less) {  // live entries other than the self-loop (reverse copies)
+        uint32_t r = 0;
+        for (int p = 0; p < k; ++p)
+            if (vv[p] > 0 && kk[p] != (uint32_t)c) ++r;
+        self_less[c] = r;
+    }
+}
+
+// Louvain form: row c of G' = the live slots of sketch(c), sorted by key.
+__global__ void k_mg_write_rows(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ vals,
+                                int64_t nc, int k, const int64_t* __restrict__ roff, int32_t* __restrict__ cols_out,
+                                uint32_t* __restrict__ w_out, Globals* glob) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t o = roff[c];
+    const int64_t m = roff[c + 1] - o;
+    for (int64_t p = 0; p < m; ++p) {
+        unsigned long long v = vals[c * k + p];
+        if (v >> 32) atomicOr(&glob->err, kErrWeightOverflow);
+        cols_out[o + p] = (int32_t)keys[c * k + p];
+        w_out[o + p] = (uint32_t)v;
+    }
+}
+
+// Leiden form, step 1: candidate entries; forward (c, d, v) of every live slot
+// at fpos[c].., then reverse (d, c, v) of every live slot with d != c at
+// R0 + rpos[c]..
+__global__ void k_mg_candidates(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ vals,
+                                int64_t nc, int k, const int64_t* __restrict__ fpos,
+                                const int64_t* __restrict__ rpos, int64_t R0, uint32_t* __restrict__ src,
+                                uint32_t* __restrict__ dst, uint32_t* __restrict__ w, Globals* glob) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int64_t f = fpos[c], r = R0 + rpos[c];
+    for (int p = 0; p < k; ++p) {
+        const unsigned long long v = vals[c * k + p];
+        if (v == 0) continue;
+        if (v >> 32) atomicOr(&glob->err, kErrWeightOverflow);
+        const uint32_t d = keys[c * k + p];
+        src[f] = (uint32_t)c; dst[f] = d; w[f] = (uint32_t)v; ++f;
+        if (d != (uint32_t)c) { src[r] = d; dst[r] = (uint32_t)c; w[r] = (uint32_t)v; ++r; }
+    }
+}
+
+// Leiden form, step 2 (entries sorted by (src, dst), forward before reverse for
+// equal keys): keep one entry per pair, the one taken from the smaller
+// community's sketch.
+__global__ void k_mg_select(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, int64_t m,
+                            uint32_t* __restrict__ keep) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    const bool same_prev = e > 0 && src[e - 1] == src[e] && dst[e - 1] == dst[e];
+    const bool same_next = e + 1 < m && src[e + 1] == src[e] && dst[e + 1] == dst[e];
+    uint32_t k = 1;
+    if (same_next) k = src[e] < dst[e] ? 1u : 0u;       // first of a pair
+    else if (same_prev) k = src[e] > dst[e] ? 1u : 0u;  // second of a pair
+    keep[e] = k;
+}
+
+__global__ void k_mg_compact(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
+                             const uint32_t* __restrict__ w, const uint32_t* __restrict__ keep,
+                             const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ cols_out,
+                             uint32_t* __restrict__ w_out, uint32_t* __restrict__ rowcnt) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m || !keep[e]) return;
+    cols_out[pos[e]] = (int32_t)dst[e];
+    w_out[pos[e]] = w[e];
+    atomicAdd(&rowcnt[src[e]], 1u);
+}
+
+cudaError_t launch_mg_sort_rows(uint32_t* keys, unsigned long long* vals, int64_t nc, int k, uint32_t* count,
+                                uint32_t* self_less, cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_mg_sort_rows<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(keys, vals, nc, k, count, self_less);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_write_rows(const uint32_t* keys, const unsigned long long* vals, int64_t nc, int k,
+                                 const int64_t* roff, int32_t* cols_out, uint32_t* w_out, Globals* glob,
+                                 cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_mg_write_rows<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(keys, vals, nc, k, roff, cols_out, w_out, glob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_candidates(const uint32_t* keys, const unsigned long long* vals, int64_t nc, int k,
+                                 const int64_t* fpos, const int64_t* rpos, int64_t R0, AggScratch& a, Globals* glob,
+                                 cudaStream_t s) {
+    if (nc == 0) return cudaSuccess;
+    k_mg_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(keys, vals, nc, k, fpos, rpos, R0, a.src, a.dst,
+                                                                  a.w, glob);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_select(const AggScratch& a, int64_t m, uint32_t* keep, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    k_mg_select<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a.src, a.dst, m, keep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_compact(const AggScratch& a, const uint32_t* keep, const uint32_t* pos, int64_t m,
+                              int32_t* cols_out, uint32_t* w_out, uint32_t* rowcnt, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    k_mg_compact<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a.src, a.dst, a.w, keep, pos, m, cols_out, w_out,
+                                                              rowcnt);
     return cudaGetLastError();
 }
 

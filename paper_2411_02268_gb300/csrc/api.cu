@@ -113,6 +113,8 @@ int check_params(const cd_params* p) {
     if (p->subtract != 0 && p->subtract != 1) return CD_EINVAL;
     if (p->one_scan != 0 && p->one_scan != 1) return CD_EINVAL;
     if (p->one_scan && p->k == 0) return CD_EINVAL;
+    if (!(p->agg_k == 0 || p->agg_k == 1 || p->agg_k == 2 || p->agg_k == 4 || p->agg_k == 8 || p->agg_k == 16))
+        return CD_EINVAL;
     if (p->sched) CD_TRY(check_schedule(p->sched));
     return CD_OK;
 }
@@ -364,6 +366,153 @@ int aggregate_level(const Level& L, const uint32_t* dense, int64_t nc, Scratch& 
     CD_CUDA(launch_segsum(a, uidx, m, cols_out, rowcnt, s));
     CD_CUDA(launch_narrow(a.wsum, m2, w_out, dglob, s));
     CD_CUDA(launch_exclusive_scan_u32_to_i64(rowcnt, off_out, nc + 1, a.tiles, &dglob->count, s));
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    if (next) {
+        *next = Level();
+        next->n = nc;
+        next->nnz = m2;
+        next->off = off_out;
+        next->cols = cols_out;
+        next->w = w_out;
+    }
+    return CD_OK;
+}
+
+// MG aggregation (Section 4.1 "aggregation phase", Fig. 3; Leiden's symmetric
+// form, Section 4.2): one k-slot sketch per community over its members' edges,
+// emitted without a second pass.  Output arrays as in aggregate_level.
+int aggregate_mg_level(const Level& L, const uint32_t* dense, int64_t nc, int k, bool symmetric, int uncond,
+                       const cd_schedule& sched, Scratch& sc, Globals* dglob, cudaStream_t s, int64_t* off_out,
+                       int32_t* cols_out, uint32_t* w_out, Level* next, int64_t cap = -1) {
+    const int64_t n = L.n, m = L.nnz;
+    // members grouped by community, ascending vertex id (stable radix sort)
+    AggScratch a;
+    CD_TRY(sc.get(&a.src, n));
+    CD_TRY(sc.get(&a.dst, n));
+    CD_TRY(sc.get(&a.w, n));
+    CD_TRY(sc.get(&a.src2, n));
+    CD_TRY(sc.get(&a.dst2, n));
+    CD_TRY(sc.get(&a.w2, n));
+    CD_TRY(sc.get(&a.hist, radix_tiles(n) * 256));
+    int64_t tiles = scan_tiles(radix_tiles(n) * 256);
+    if (scan_tiles(nc + 1) > tiles) tiles = scan_tiles(nc + 1);
+    if (scan_tiles(2 * nc * k + 1) > tiles) tiles = scan_tiles(2 * nc * k + 1);
+    CD_TRY(sc.get(&a.tiles, tiles + 1));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(cudaMemcpyAsync(a.src, dense, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    CD_CUDA(launch_iota(a.dst, n, s));
+    CD_CUDA(launch_iota(a.w, n, s));
+    CD_CUDA(radix_sort_keys(a, n, bits_for(nc), 0, dglob, s));
+    const uint32_t* members = a.dst;
+    // member ranges and entry counts per community
+    uint32_t *cnt, *ecnt;
+    int64_t *moff, *coff;
+    CD_TRY(sc.get(&cnt, nc + 1));
+    CD_TRY(sc.get(&ecnt, nc + 1));
+    CD_TRY(sc.get(&moff, nc + 1));
+    CD_TRY(sc.get(&coff, nc + 1));
+    CD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (nc + 1), s));
+    CD_CUDA(cudaMemsetAsync(ecnt, 0, sizeof(uint32_t) * (nc + 1), s));
+    CD_CUDA(launch_community_counts(L.off, dense, n, cnt, ecnt, s));
+    CD_CUDA(launch_exclusive_scan_u32_to_i64(cnt, moff, nc + 1, a.tiles, &dglob->count, s));
+    CD_CUDA(launch_exclusive_scan_u32_to_i64(ecnt, coff, nc + 1, a.tiles, &dglob->count, s));
+    // communities bucketed by their entry count
+    Level C;
+    C.n = nc;
+    C.nnz = m;
+    C.off = coff;
+    C.bt = table_from(sched);
+    C.colors = 1;
+    const int nkeys = C.bt.nb;
+    int64_t ntiles = bucket_tiles(nc);
+    uint32_t *tc, *to;
+    int64_t* starts;
+    CD_TRY(sc.get(&C.verts, nc));
+    CD_TRY(sc.get(&tc, ntiles * nkeys));
+    CD_TRY(sc.get(&to, ntiles * nkeys));
+    CD_TRY(sc.get(&starts, nkeys + 1));
+    CD_CUDA(launch_bucket(coff, nc, m, C.bt, 1, tc, to, starts, C.verts, nullptr, nullptr, dglob, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
+    C.starts.assign(hg.starts, hg.starts + nkeys + 1);
+    C.bt = C.table_for(0);
+    // one sketch per community
+    uint32_t* keys;
+    unsigned long long* vals;
+    CD_TRY(sc.get(&keys, nc * k));
+    CD_TRY(sc.get(&vals, nc * k));
+    CD_CUDA(cudaMemsetAsync(keys, 0xFF, sizeof(uint32_t) * nc * k, s));
+    CD_CUDA(cudaMemsetAsync(vals, 0, sizeof(unsigned long long) * nc * k, s));
+    AggArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.a.off = L.off; g.a.cols = L.cols; g.a.w = L.w; g.a.labels = dense;
+    g.a.glob = dglob; g.a.verts = C.verts; g.a.n = n; g.a.nnz = m; g.a.uncond = uncond; g.a.bt = C.bt;
+    g.moff = moff; g.members = members; g.out_keys = keys; g.out_vals = vals;
+    CD_CUDA(launch_agg_mg(g, k, L.two_m >= (1ull << 32), C.bt.bbegin[C.bt.nb], s));
+    // rows
+    uint32_t *count, *self_less;
+    CD_TRY(sc.get(&count, nc + 1));
+    CD_TRY(sc.get(&self_less, nc + 1));
+    CD_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t) * (nc + 1), s));
+    CD_CUDA(cudaMemsetAsync(self_less, 0, sizeof(uint32_t) * (nc + 1), s));
+    CD_CUDA(launch_mg_sort_rows(keys, vals, nc, k, count, symmetric ? self_less : nullptr, s));
+    int64_t m2 = 0;
+    if (!symmetric) {
+        int64_t* roff;
+        CD_TRY(sc.get(&roff, nc + 1));
+        CD_CUDA(launch_exclusive_scan_u32_to_i64(count, roff, nc + 1, a.tiles, &dglob->count, s));
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        m2 = (int64_t)hg.g.count;
+        if (cap >= 0 && m2 > cap) return CD_EINVAL;
+        if (!off_out) {
+            CD_TRY(sc.get(&off_out, nc + 1));
+            CD_TRY(sc.get(&cols_out, m2));
+            CD_TRY(sc.get(&w_out, m2));
+        }
+        CD_CUDA(launch_mg_write_rows(keys, vals, nc, k, roff, cols_out, w_out, dglob, s));
+        CD_CUDA(cudaMemcpyAsync(off_out, roff, sizeof(int64_t) * (nc + 1), cudaMemcpyDeviceToDevice, s));
+    } else {
+        int64_t *fpos, *rpos;
+        CD_TRY(sc.get(&fpos, nc + 1));
+        CD_TRY(sc.get(&rpos, nc + 1));
+        CD_CUDA(launch_exclusive_scan_u32_to_i64(count, fpos, nc + 1, a.tiles, &dglob->count, s));
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        const int64_t F = (int64_t)hg.g.count;
+        CD_CUDA(launch_exclusive_scan_u32_to_i64(self_less, rpos, nc + 1, a.tiles, &dglob->count, s));
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        const int64_t M = F + (int64_t)hg.g.count;
+        AggScratch b;
+        CD_TRY(sc.get(&b.src, M));
+        CD_TRY(sc.get(&b.dst, M));
+        CD_TRY(sc.get(&b.w, M));
+        CD_TRY(sc.get(&b.src2, M));
+        CD_TRY(sc.get(&b.dst2, M));
+        CD_TRY(sc.get(&b.w2, M));
+        CD_TRY(sc.get(&b.hist, radix_tiles(M) * 256));
+        int64_t bt = scan_tiles(radix_tiles(M) * 256);
+        if (scan_tiles(M + 1) > bt) bt = scan_tiles(M + 1);
+        if (scan_tiles(nc + 1) > bt) bt = scan_tiles(nc + 1);
+        CD_TRY(sc.get(&b.tiles, bt + 1));
+        CD_CUDA(launch_mg_candidates(keys, vals, nc, k, fpos, rpos, F, b, dglob, s));
+        CD_CUDA(radix_sort_pairs(b, M, nc, dglob, s));
+        uint32_t *keep, *pos, *rowcnt;
+        CD_TRY(sc.get(&keep, M));
+        CD_TRY(sc.get(&pos, M));
+        CD_TRY(sc.get(&rowcnt, nc + 1));
+        CD_CUDA(launch_mg_select(b, M, keep, s));
+        CD_CUDA(launch_exclusive_scan_u32(keep, pos, M, b.tiles, &dglob->count, s));
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        m2 = (int64_t)hg.g.count;
+        if (cap >= 0 && m2 > cap) return CD_EINVAL;
+        if (!off_out) {
+            CD_TRY(sc.get(&off_out, nc + 1));
+            CD_TRY(sc.get(&cols_out, m2));
+            CD_TRY(sc.get(&w_out, m2));
+        }
+        CD_CUDA(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * (nc + 1), s));
+        CD_CUDA(launch_mg_compact(b, keep, pos, M, cols_out, w_out, rowcnt, s));
+        CD_CUDA(launch_exclusive_scan_u32_to_i64(rowcnt, off_out, nc + 1, b.tiles, &dglob->count, s));
+    }
     CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
     if (next) {
         *next = Level();
@@ -742,7 +891,11 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
         if (nc == cur.n || (double)nc > p->aggregation_tolerance * (double)cur.n) break;
         if (pass + 1 >= p->max_passes) break;
         Level next;
-        CD_TRY(aggregate_level(cur, dense, nc, sc, dglob, s, nullptr, nullptr, nullptr, &next));
+        if (p->agg_k > 0)
+            CD_TRY(aggregate_mg_level(cur, dense, nc, p->agg_k, false, p->subtract, sched, sc, dglob, s, nullptr,
+                                      nullptr, nullptr, &next));
+        else
+            CD_TRY(aggregate_level(cur, dense, nc, sc, dglob, s, nullptr, nullptr, nullptr, &next));
         cur = next;
         tol /= p->tolerance_drop;
     }
@@ -839,7 +992,11 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
         CD_CUDA(launch_scatter_bound(dr, dc, cur.n, next_init, s));
         CD_CUDA(launch_compose(top, in.n, dr, s));
         Level next;
-        CD_TRY(aggregate_level(cur, dr, nr, sc, dglob, s, nullptr, nullptr, nullptr, &next));
+        if (p->agg_k > 0)
+            CD_TRY(aggregate_mg_level(cur, dr, nr, p->agg_k, true, p->subtract, sched, sc, dglob, s, nullptr,
+                                      nullptr, nullptr, &next));
+        else
+            CD_TRY(aggregate_level(cur, dr, nr, sc, dglob, s, nullptr, nullptr, nullptr, &next));
         cur = next;
         init = next_init;
         tol /= p->tolerance_drop;
@@ -849,6 +1006,48 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
     CD_TRY(modularity_of(in, result, sc, dglob, s, &q));
     CD_TRY(emit_labels(g, result, labels_out, s));
     if (q_out) *q_out = q;
+    return CD_OK;
+}
+
+int cd_aggregate_mg(const cd_csr* g, const uint32_t* labels, int k, int subtract, int symmetric,
+                    const cd_schedule* schedp, void* stream, uint32_t* dense_out, int64_t* offsets_out,
+                    int32_t* cols_out, uint32_t* weights_out, int64_t* n_out, int64_t* nnz_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    if (g->memory != CD_MEM_DEVICE) return CD_EINVAL;
+    if (!(k == 1 || k == 2 || k == 4 || k == 8 || k == 16) || (subtract != 0 && subtract != 1)) return CD_EINVAL;
+    if (!labels || !dense_out || !offsets_out || !n_out || !nnz_out) return CD_EINVAL;
+    if (g->n > 0 && (!cols_out || !weights_out)) return CD_EINVAL;
+    cd_schedule sched;
+    if (schedp) { CD_TRY(check_schedule(schedp)); sched = *schedp; } else default_schedule(&sched);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level L;
+    CD_TRY(input_level(g, sc, &L));
+    // 2m for the sketch width
+    uint64_t* K;
+    CD_TRY(sc.get(&K, L.n));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, K, dglob, s));
+    uint64_t* Sig;
+    uint32_t* sz;
+    CD_TRY(sc.get(&Sig, L.n));
+    CD_TRY(sc.get(&sz, L.n));
+    CD_CUDA(launch_totals(labels, K, L.n, Sig, sz, dglob, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    L.two_m = hg.g.two_m;
+    int64_t nc = 0;
+    CD_TRY(renumber_level(L, labels, dense_out, sc, dglob, &nc, s));
+    Level next;
+    CD_TRY(aggregate_mg_level(L, dense_out, nc, k, symmetric != 0, subtract, sched, sc, dglob, s, offsets_out,
+                              cols_out, weights_out, &next, g->nnz));
+    CD_CUDA(cudaStreamSynchronize(s));
+    *n_out = next.n;
+    *nnz_out = next.nnz;
+    g_stats.communities = nc;
     return CD_OK;
 }
 

@@ -64,6 +64,16 @@ struct SweepArgs {
     BucketTable bt;
 };
 
+// MG aggregation: communities are the rows (buckets over communities in
+// a.verts/a.bt, member ranges in moff/members, dense ids in a.labels).
+struct AggArgs {
+    SweepArgs a;
+    const int64_t* moff;      // nc + 1
+    const uint32_t* members;  // vertex ids grouped by community, ascending
+    uint32_t* out_keys;       // nc * k
+    unsigned long long* out_vals;
+};
+
 // Colour class of vertex v among `colors` classes: the 32-bit integer hash
 // "lowbias32" (C. Wellons) of v, modulo the number of classes.
 __host__ __device__ __forceinline__ uint32_t color_of(uint32_t v, int colors) {
@@ -101,6 +111,7 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s);
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
+cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, cudaStream_t s);
 cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in,
                           const uint32_t* labels_out, const uint64_t* K, int64_t n,
                           uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s);
@@ -146,6 +157,21 @@ struct AggScratch {
 cudaError_t launch_expand(const int64_t* off, const int32_t* cols, int64_t n, int64_t nnz, const uint32_t* dense,
                           uint32_t* src, uint32_t* dst, cudaStream_t s);
 cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* glob, cudaStream_t s);
+cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_dst, Globals* glob, cudaStream_t s);
+int bits_for(int64_t nc);
+cudaError_t launch_community_counts(const int64_t* off, const uint32_t* dense, int64_t n, uint32_t* cnt,
+                                    uint32_t* ecnt, cudaStream_t s);
+cudaError_t launch_mg_sort_rows(uint32_t* keys, unsigned long long* vals, int64_t nc, int k, uint32_t* count,
+                                uint32_t* self_less, cudaStream_t s);
+cudaError_t launch_mg_write_rows(const uint32_t* keys, const unsigned long long* vals, int64_t nc, int k,
+                                 const int64_t* roff, int32_t* cols_out, uint32_t* w_out, Globals* glob,
+                                 cudaStream_t s);
+cudaError_t launch_mg_candidates(const uint32_t* keys, const unsigned long long* vals, int64_t nc, int k,
+                                 const int64_t* fpos, const int64_t* rpos, int64_t R0, AggScratch& a, Globals* glob,
+                                 cudaStream_t s);
+cudaError_t launch_mg_select(const AggScratch& a, int64_t m, uint32_t* keep, cudaStream_t s);
+cudaError_t launch_mg_compact(const AggScratch& a, const uint32_t* keep, const uint32_t* pos, int64_t m,
+                              int32_t* cols_out, uint32_t* w_out, uint32_t* rowcnt, cudaStream_t s);
 cudaError_t launch_heads(const AggScratch& a, int64_t nnz, cudaStream_t s);
 cudaError_t launch_segsum(const AggScratch& a, const uint32_t* uidx, int64_t nnz, int32_t* cols_out,
                           uint32_t* rowcnt, cudaStream_t s);

@@ -240,6 +240,24 @@ extern template cudaError_t launch_k<2>(const SweepArgs&, bool, int64_t, cudaStr
 extern template cudaError_t launch_k<4>(const SweepArgs&, bool, int64_t, cudaStream_t);
 extern template cudaError_t launch_k<8>(const SweepArgs&, bool, int64_t, cudaStream_t);
 extern template cudaError_t launch_k<16>(const SweepArgs&, bool, int64_t, cudaStream_t);
+template <int K>
+cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStream_t s);
+extern template cudaError_t launch_agg_k<1>(const AggArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_agg_k<2>(const AggArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_agg_k<4>(const AggArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_agg_k<8>(const AggArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_agg_k<16>(const AggArgs&, bool, int64_t, cudaStream_t);
+
+cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, cudaStream_t s) {
+    switch (k) {
+        case 1: return launch_agg_k<1>(g, wide, nblocks, s);
+        case 2: return launch_agg_k<2>(g, wide, nblocks, s);
+        case 4: return launch_agg_k<4>(g, wide, nblocks, s);
+        case 8: return launch_agg_k<8>(g, wide, nblocks, s);
+        case 16: return launch_agg_k<16>(g, wide, nblocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s) {
     if (nblocks == 0) return cudaSuccess;

@@ -1,6 +1,7 @@
-// MG-sketch sweep kernel for sketch size k = 1.
+// MG-sketch sweep and MG-aggregation kernels for sketch size k = 1.
 #include "sweep_mg.cuh"
 
 namespace cdk {
 template cudaError_t launch_k<1>(const SweepArgs&, bool, int64_t, cudaStream_t);
+template cudaError_t launch_agg_k<1>(const AggArgs&, bool, int64_t, cudaStream_t);
 }  // namespace cdk

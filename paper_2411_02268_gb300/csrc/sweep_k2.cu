@@ -1,6 +1,7 @@
-// MG-sketch sweep kernel for sketch size k = 2.
+// MG-sketch sweep and MG-aggregation kernels for sketch size k = 2.
 #include "sweep_mg.cuh"
 
 namespace cdk {
 template cudaError_t launch_k<2>(const SweepArgs&, bool, int64_t, cudaStream_t);
+template cudaError_t launch_agg_k<2>(const AggArgs&, bool, int64_t, cudaStream_t);
 }  // namespace cdk

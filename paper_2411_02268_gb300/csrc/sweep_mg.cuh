@@ -204,6 +204,24 @@ __device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk
     s.lossy |= plossy;
 }
 
+// Merge tree over the G streams of a group inside one warp: S[s] <- merge(S[s],
+// S[s+o]) for o = G/2 .. 1; lane 0 ends with the row's sketch.
+template <int G, int K, typename VT>
+__device__ __forceinline__ void group_merge(Sketch<K, VT>& sk, int lane, unsigned gmask, bool unc) {
+#pragma unroll 1
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        uint32_t pk[K];
+        VT pv[K];
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            pk[p] = __shfl_down_sync(gmask, sk.key[p], o, G);
+            pv[p] = __shfl_down_sync(gmask, sk.value(p), o, G);
+        }
+        const bool pl = __shfl_down_sync(gmask, (int)sk.lossy, o, G) != 0;
+        if (lane < o) merge_into(sk, pk, pv, pl, unc);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // G streams per vertex inside one warp (G = 1, 2, ..., 32).
 // ---------------------------------------------------------------------------
@@ -239,19 +257,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
             scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
         }
     }
-    // merge tree: S[s] <- merge(S[s], S[s+o]), o = G/2 .. 1
-#pragma unroll 1
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        uint32_t pk[K];
-        VT pv[K];
-#pragma unroll
-        for (int p = 0; p < K; ++p) {
-            pk[p] = __shfl_down_sync(gmask, sk.key[p], o, G);
-            pv[p] = __shfl_down_sync(gmask, sk.value(p), o, G);
-        }
-        const bool pl = __shfl_down_sync(gmask, (int)sk.lossy, o, G) != 0;
-        if (lane < o) merge_into(sk, pk, pv, pl, unc);
-    }
+    group_merge<G, K, VT>(sk, lane, gmask, unc);
     // candidates (and, if the sketch never subtracted, their exact weights)
     uint32_t cand[K];
     VT acc[K];
@@ -325,6 +331,39 @@ __device__ __forceinline__ void sub_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Merge tree over the L = 64..256 streams of a sub-block: cross-warp rounds
+// (o = L/2 .. 32) through shared memory, then in-warp rounds (o = 16 .. 1) in
+// the sub-block's first warp; thread s = 0 ends with the row's sketch.
+template <int L, int K, typename VT>
+__device__ __forceinline__ void block_merge(Sketch<K, VT>& sk, int s, int sb, int bar, BlockSmem<K, VT>& sm,
+                                            bool unc) {
+    const int slot_base = sb * (L / 2);  // (256/L) sub-blocks x L/2 slots = 128
+#pragma unroll 1
+    for (int o = L / 2; o >= 32; o >>= 1) {
+        if (s >= o && s < 2 * o) {
+#pragma unroll
+            for (int p = 0; p < K; ++p) {
+                sm.k[slot_base + s - o][p] = sk.key[p];
+                sm.v[slot_base + s - o][p] = sk.value(p);
+            }
+            sm.lossy[slot_base + s - o] = (int)sk.lossy;
+        }
+        sub_barrier(bar, L);
+        if (s < o) {
+            uint32_t pk[K];
+            VT pv[K];
+#pragma unroll
+            for (int p = 0; p < K; ++p) {
+                pk[p] = sm.k[slot_base + s][p];
+                pv[p] = sm.v[slot_base + s][p];
+            }
+            merge_into(sk, pk, pv, sm.lossy[slot_base + s] != 0, unc);
+        }
+        sub_barrier(bar, L);
+    }
+    if ((s >> 5) == 0) group_merge<32, K, VT>(sk, s & 31, 0xffffffffu, unc);
+}
+
 template <int L, int K, typename VT>
 __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bool valid,
                                               BlockSmem<K, VT>& sm) {
@@ -357,54 +396,15 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     if (act) {
         scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
     }
-    // cross-warp rounds through shared memory (o = L/2 .. 32)
-    const int slot_base = sb * (L / 2);  // (256/L) sub-blocks x L/2 slots = 128
-#pragma unroll 1
-    for (int o = L / 2; o >= 32; o >>= 1) {
-        if (s >= o && s < 2 * o) {
+    block_merge<L, K, VT>(sk, s, sb, bar, sm, unc);
+    if (wl == 0 && lane == 0) {
 #pragma unroll
-            for (int p = 0; p < K; ++p) {
-                sm.k[slot_base + s - o][p] = sk.key[p];
-                sm.v[slot_base + s - o][p] = sk.value(p);
-            }
-            sm.lossy[slot_base + s - o] = (int)sk.lossy;
+        for (int p = 0; p < K; ++p) {
+            const VT v = sk.value(p);
+            sm.cand[sb][p] = v > 0 ? sk.key[p] : kEmpty;
+            sm.cval[sb][p] = v;
         }
-        sub_barrier(bar, L);
-        if (s < o) {
-            uint32_t pk[K];
-            VT pv[K];
-#pragma unroll
-            for (int p = 0; p < K; ++p) {
-                pk[p] = sm.k[slot_base + s][p];
-                pv[p] = sm.v[slot_base + s][p];
-            }
-            merge_into(sk, pk, pv, sm.lossy[slot_base + s] != 0, unc);
-        }
-        sub_barrier(bar, L);
-    }
-    // in-warp rounds (o = 16 .. 1) in the first warp of the sub-block
-    if (wl == 0) {
-#pragma unroll 1
-        for (int o = 16; o >= 1; o >>= 1) {
-            uint32_t pk[K];
-            VT pv[K];
-#pragma unroll
-            for (int p = 0; p < K; ++p) {
-                pk[p] = __shfl_down_sync(0xffffffffu, sk.key[p], o);
-                pv[p] = __shfl_down_sync(0xffffffffu, sk.value(p), o);
-            }
-            const bool pl = __shfl_down_sync(0xffffffffu, (int)sk.lossy, o) != 0;
-            if (lane < o) merge_into(sk, pk, pv, pl, unc);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int p = 0; p < K; ++p) {
-                const VT v = sk.value(p);
-                sm.cand[sb][p] = v > 0 ? sk.key[p] : kEmpty;
-                sm.cval[sb][p] = v;
-            }
-            sm.exact[sb] = sk.lossy ? 0 : 1;
-        }
+        sm.exact[sb] = sk.lossy ? 0 : 1;
     }
     sub_barrier(bar, L);
     uint32_t cand[K];
@@ -522,6 +522,106 @@ __global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) 
         default: o = block_body<256, K, VT>(a, vi, valid, sm); break;
     }
     epilogue(a, o);
+}
+
+// ---------------------------------------------------------------------------
+// MG aggregation (Section 4.1, "aggregation phase"; Fig. 3): one sketch per
+// community over the edges of all its members (ascending vertex id, each row
+// in CSR order, self-loops kept), streams and merge tree as in the sweep;
+// no second pass.  The community's sketch is written to out_keys/out_vals
+// (K slots per community).  a.labels holds the dense community ids; the
+// buckets list communities, a.off gives their member ranges in `members`.
+// ---------------------------------------------------------------------------
+template <int K, typename VT, typename F>
+__device__ __forceinline__ void for_members(const AggArgs& g, uint32_t c, int lane, int L, F&& f) {
+    for (int64_t q = g.moff[c]; q < g.moff[c + 1]; ++q) {
+        const uint32_t m = g.members[q];
+        const int64_t start = g.a.off[m], end = g.a.off[m + 1];
+        if (L == 1) {
+            for_row(g.a, start, end, kEmpty, 0u, f);
+        } else {
+            const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
+            const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (L - 1))) & (L - 1));
+            scan_chunks(g.a, first, c1, L, start, end, kEmpty, 0u, f);
+        }
+    }
+}
+
+template <int K, typename VT>
+__device__ __forceinline__ void agg_store(const AggArgs& g, uint32_t c, const Sketch<K, VT>& sk) {
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        const VT v = sk.value(p);
+        g.out_keys[(size_t)c * K + p] = v > 0 ? sk.key[p] : kEmpty;
+        g.out_vals[(size_t)c * K + p] = (unsigned long long)v;
+    }
+}
+
+template <int G, int K, typename VT>
+__device__ __forceinline__ void agg_group(const AggArgs& g, int64_t vi, bool valid) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu
+                                     : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    const bool unc = g.a.uncond != 0;
+    Sketch<K, VT> sk;
+    sk.init();
+    uint32_t c = 0;
+    if (valid) {
+        c = g.a.verts[vi];
+        for_members<K, VT>(g, c, lane, G, [&](uint32_t key, uint32_t w) { sk.update(key, (VT)w, unc); });
+    }
+    group_merge<G, K, VT>(sk, lane, gmask, unc);
+    if (valid && lane == 0) agg_store(g, c, sk);
+}
+
+template <int L, int K, typename VT>
+__device__ __forceinline__ void agg_block(const AggArgs& g, int64_t vi, bool valid, BlockSmem<K, VT>& sm) {
+    const int sb = threadIdx.x / L;
+    const int s = threadIdx.x % L;
+    const bool unc = g.a.uncond != 0;
+    Sketch<K, VT> sk;
+    sk.init();
+    uint32_t c = 0;
+    if (valid) {
+        c = g.a.verts[vi];
+        for_members<K, VT>(g, c, s, L, [&](uint32_t key, uint32_t w) { sk.update(key, (VT)w, unc); });
+    }
+    block_merge<L, K, VT>(sk, s, sb, 1 + sb, sm, unc);
+    if (valid && s == 0) agg_store(g, c, sk);
+}
+
+template <int K, typename VT>
+__global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) k_agg_mg(const AggArgs g) {
+    __shared__ BlockSmem<K, VT> sm;
+    const int64_t blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
+    int b = 0;
+#pragma unroll
+    for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+        if (q < g.a.bt.nb && blk >= g.a.bt.bbegin[q]) b = q;
+    const int L = g.a.bt.lanes[b];
+    const int64_t lb = blk - g.a.bt.bbegin[b];
+    const int vpb = L >= kBlock ? 1 : kBlock / L;
+    const int64_t vi = g.a.bt.vbegin[b] + lb * vpb + threadIdx.x / L;
+    const bool valid = vi < g.a.bt.vbegin[b + 1];
+    switch (L) {
+        case 1: agg_group<1, K, VT>(g, vi, valid); break;
+        case 2: agg_group<2, K, VT>(g, vi, valid); break;
+        case 4: agg_group<4, K, VT>(g, vi, valid); break;
+        case 8: agg_group<8, K, VT>(g, vi, valid); break;
+        case 16: agg_group<16, K, VT>(g, vi, valid); break;
+        case 32: agg_group<32, K, VT>(g, vi, valid); break;
+        case 64: agg_block<64, K, VT>(g, vi, valid, sm); break;
+        case 128: agg_block<128, K, VT>(g, vi, valid, sm); break;
+        default: agg_block<256, K, VT>(g, vi, valid, sm); break;
+    }
+}
+
+template <int K>
+cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStream_t s) {
+    if (nblocks == 0) return cudaSuccess;
+    if (wide) k_agg_mg<K, unsigned long long><<<(unsigned)nblocks, kBlock, 0, s>>>(g);
+    else k_agg_mg<K, uint32_t><<<(unsigned)nblocks, kBlock, 0, s>>>(g);
+    return cudaGetLastError();
 }
 
 template <int K>

@@ -166,3 +166,36 @@ def test_lpa_one_scan_bit_exact_with_twin(env, gname):
     assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)
     with pytest.raises(cd.CDError):
         cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=8, one_scan=True))
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k,sym", [(8, False), (4, True), (16, True), (2, False)])
+def test_aggregate_mg_matches_oracle(env, gname, k, sym):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    rng = np.random.default_rng(5)
+    sched = cd.cd_default_schedule(8)
+    for lab in (rng.integers(0, max(2, g.n // 9), g.n).astype(np.uint32),
+                (np.arange(g.n) // 40).astype(np.uint32), np.zeros(g.n, np.uint32)):
+        G = cd.Graph.to_device(g)
+        dense, G2 = cd.cd_aggregate_mg(G, torch.from_numpy(lab.view(np.int32)).cuda(), k=k, symmetric=sym,
+                                       schedule=sched)
+        R2, rdense = oracle.aggregate_mg(g, lab, k, False, sched_of(cd, 8), symmetric=sym)
+        assert np.array_equal(dense.cpu().numpy().view(np.uint32), rdense)
+        assert G2.n == R2.n
+        assert np.array_equal(G2.offsets.cpu().numpy(), R2.offsets)
+        assert np.array_equal(G2.cols.cpu().numpy(), R2.cols)
+        assert np.array_equal(G2.weights.cpu().numpy().view(np.uint32), R2.w)
+
+
+@pytest.mark.parametrize("gname", ["sbm10k", "rmat13", "grid60"])
+def test_louvain_leiden_with_mg_aggregation(env, gname):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    G = cd.Graph.to_device(g)
+    lab, q = cd.cd_louvain(G, cd.make_params(k=8, agg_k=8))
+    ref = oracle.louvain_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)
+    lab, q2 = cd.cd_leiden(G, cd.make_params(k=8, agg_k=8))
+    ref = oracle.leiden_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)

@@ -493,3 +493,31 @@ def test_leiden_quality_and_bounds():
         if t.nnz:
             qstar, _ = oracle.brute_force_best(t)
             assert oracle.modularity_fraction(t, oracle.leiden_sync(t, k=8, tol=0.0)) <= qstar
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_mg_aggregation_pins(seed):
+    """MG aggregation (Section 4.1, Fig. 3): equals the exact super-graph when
+    every community links to at most k communities; otherwise its weights
+    never exceed the exact ones (clamped subtraction only lowers values) and
+    the symmetric (Leiden) form is symmetric."""
+    g = gen.sbm(600, 12, 0.2, 0.01, wmax=7, seed=seed)
+    coarse = (np.arange(g.n) // 100).astype(np.uint32)       # 6 communities
+    exact, _ = oracle.aggregate(g, coarse)
+    mg, _ = oracle.aggregate_mg(g, coarse, k=8)
+    assert np.array_equal(exact.offsets, mg.offsets) and np.array_equal(exact.cols, mg.cols)
+    assert np.array_equal(exact.w, mg.w)
+    fine = (np.arange(g.n) // 10).astype(np.uint32)          # 60 communities
+    exact, _ = oracle.aggregate(g, fine)
+    ex = {(r, int(exact.cols[e])): int(exact.w[e]) for r in range(exact.n)
+          for e in range(exact.offsets[r], exact.offsets[r + 1])}
+    for sym in (False, True):
+        mg, _ = oracle.aggregate_mg(g, fine, k=4, symmetric=sym)
+        got = {(r, int(mg.cols[e])): int(mg.w[e]) for r in range(mg.n)
+               for e in range(mg.offsets[r], mg.offsets[r + 1])}
+        for key, val in got.items():
+            assert 0 < val <= ex[key]
+        if sym:
+            assert all(got.get((b, a)) == v for (a, b), v in got.items())
+        else:
+            assert all(mg.offsets[r + 1] - mg.offsets[r] <= 4 for r in range(mg.n))
