@@ -155,9 +155,7 @@ def oracle_sample(g, k: int, seconds: float, threads: int):
     `seconds` of CPU work; returns (entries swept per second, description)."""
     import oracle
     from paper_2411_02268_gb300 import cd
-    sched = oracle.Schedule(*cd.cd_default_schedule(k).as_lists()) if os.path.exists(cd.SO) else \
-        oracle.Schedule([2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 32768, 2**62],
-                        [1, 1, 1, 1, 1, 2, 2, 4, 4, 8, 8, 16, 32, 128, 256], 4)
+    sched = oracle.Schedule(*cd.cd_default_schedule(k).as_lists())
     K = oracle.degrees(g)
     labels = np.arange(g.n, dtype=np.uint32)
     Sig, size = oracle.community_totals(g.n, labels, K)

@@ -475,7 +475,7 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
 
 
 def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
-                 agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0):
+                 agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0, agg_sched=None):
     """Louvain with colour-class sub-sweeps: the exact schedule of cd_louvain
     (agg_k > 0: MG aggregation with agg_k slots)."""
     sched = sched or Schedule.single_stream()
@@ -490,7 +490,7 @@ def louvain_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, m
         if nc == cur.n or nc > agg_tol * cur.n or p + 1 >= max_passes:
             break
         if agg_k > 0:
-            cur, _ = aggregate_mg(cur, dense, agg_k, uncond, sched)
+            cur, _ = aggregate_mg(cur, dense, agg_k, uncond, agg_sched or sched)
         else:
             cur, _ = aggregate(cur, dense)
         tol /= tol_drop
@@ -526,7 +526,7 @@ def refine_sync(g, bound, k=8, uncond=False, sched=None, threads=1, colors=8):
 
 
 def leiden_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, max_passes=10,
-                agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0):
+                agg_tol=0.8, sched=None, threads=1, colors=8, agg_k=0, agg_sched=None):
     """Leiden (Section 3.4): local-moving (from the previous level's bounds),
     refinement within the communities found, aggregation by the refined
     partition, repeated; the result is the last level's communities mapped
@@ -551,7 +551,7 @@ def leiden_sync(g, k=8, uncond=False, tol=0.01, tol_drop=10.0, max_sweeps=20, ma
         nxt[dr] = dc
         top = dr[top]
         if agg_k > 0:
-            cur, _ = aggregate_mg(cur, dr, agg_k, uncond, sched, symmetric=True)
+            cur, _ = aggregate_mg(cur, dr, agg_k, uncond, agg_sched or sched, symmetric=True)
         else:
             cur, _ = aggregate(cur, dr)
         init = nxt

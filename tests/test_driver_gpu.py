@@ -174,13 +174,13 @@ def test_aggregate_mg_matches_oracle(env, gname, k, sym):
     cd, torch = env
     g = GRAPHS[gname]()
     rng = np.random.default_rng(5)
-    sched = cd.cd_default_schedule(8)
+    sched = cd.cd_default_schedule(16)      # MG aggregation runs one lane per stream
     for lab in (rng.integers(0, max(2, g.n // 9), g.n).astype(np.uint32),
                 (np.arange(g.n) // 40).astype(np.uint32), np.zeros(g.n, np.uint32)):
         G = cd.Graph.to_device(g)
         dense, G2 = cd.cd_aggregate_mg(G, torch.from_numpy(lab.view(np.int32)).cuda(), k=k, symmetric=sym,
                                        schedule=sched)
-        R2, rdense = oracle.aggregate_mg(g, lab, k, False, sched_of(cd, 8), symmetric=sym)
+        R2, rdense = oracle.aggregate_mg(g, lab, k, False, sched_of(cd, 16), symmetric=sym)
         assert np.array_equal(dense.cpu().numpy().view(np.uint32), rdense)
         assert G2.n == R2.n
         assert np.array_equal(G2.offsets.cpu().numpy(), R2.offsets)
@@ -194,8 +194,8 @@ def test_louvain_leiden_with_mg_aggregation(env, gname):
     g = GRAPHS[gname]()
     G = cd.Graph.to_device(g)
     lab, q = cd.cd_louvain(G, cd.make_params(k=8, agg_k=8))
-    ref = oracle.louvain_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8)
+    ref = oracle.louvain_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8, agg_sched=sched_of(cd, 16))
     assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)
     lab, q2 = cd.cd_leiden(G, cd.make_params(k=8, agg_k=8))
-    ref = oracle.leiden_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8)
+    ref = oracle.leiden_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8, agg_sched=sched_of(cd, 16))
     assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)

@@ -30,6 +30,11 @@ WIDE = ([2**62], [256])
 MID = ([3, 40, 2**62], [1, 32, 64])
 
 
+def sched_for(cd, k, deg, lanes):
+    """A test schedule with the kernel's chunk width (the default's vec)."""
+    return cd.schedule_from(deg, lanes, cd.cd_default_schedule(k).vec)
+
+
 def oracle_sched(cd, sched):
     deg, lanes, vec = sched.as_lists()
     return oracle.Schedule(deg, lanes, vec)
@@ -86,7 +91,7 @@ GRAPHS = {
 
 
 @pytest.mark.parametrize("gname", list(GRAPHS))
-@pytest.mark.parametrize("k", [8, 1, 4, 16])
+@pytest.mark.parametrize("k", [8, 1, 2, 4, 16])
 def test_mg_louvain_default_schedule(env, gname, k):
     cd, torch = env
     g = GRAPHS[gname]()
@@ -96,12 +101,12 @@ def test_mg_louvain_default_schedule(env, gname, k):
 
 @pytest.mark.parametrize("gname", ["rmat12_w16", "ragged_loops", "sbm10k"])
 @pytest.mark.parametrize("sched_name", ["all_lanes", "wide", "mid"])
-@pytest.mark.parametrize("k", [2, 8, 16])
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
 def test_mg_all_stream_schedules(env, gname, sched_name, k):
     cd, torch = env
     g = GRAPHS[gname]()
     deg, lanes = {"all_lanes": ALL_LANES, "wide": WIDE, "mid": MID}[sched_name]
-    s = cd.schedule_from(deg, lanes)
+    s = sched_for(cd, k, deg, lanes)
     for _, lab in label_states(g, 2):
         check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, sched=s)
         check(cd, torch, g, lab, oracle.MODE_LPA, k, sched=s)
@@ -112,7 +117,7 @@ def test_mg_all_stream_schedules(env, gname, sched_name, k):
 def test_mg_lpa_and_unconditional(env, gname, k):
     cd, torch = env
     g = GRAPHS[gname]()
-    s = cd.schedule_from(*ALL_LANES)
+    s = sched_for(cd, k, *ALL_LANES)
     for _, lab in label_states(g, 3):
         check(cd, torch, g, lab, oracle.MODE_LPA, k)
         check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, uncond=1)
