@@ -12,56 +12,52 @@
 namespace cdk {
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 on a register-resident sketch of K slots.
-//
-// The slot values are kept as t[p] against a per-sketch subtraction total D:
-// the value of slot p is max(t[p] - D, 0).  Subtracting w from every slot
-// (clamped at 0) is then D += w, because clamped subtractions compose
-// (max(max(v - a, 0) - b, 0) = max(v - a - b, 0)); adding w to slot p is
-// t[p] = max(t[p], D) + w; slot p is empty iff t[p] <= D; inserting sets
-// t[p] = D + w.  The values (and so every result) are exactly those of
-// Algorithm 1.  t and D never exceed the row's weighted degree.
-// `lossy` records whether anything was ever subtracted: a sketch that never
-// subtracted holds every community it saw with its exact weight.
+// Algorithm 1 on a register-resident sketch of K slots: key[p], value t[p]
+// (0 = empty).  `lossy` records whether anything was ever subtracted: a
+// sketch that never subtracted holds every community it saw with its exact
+// weight, so the second scan can be skipped.  (Keeping the values against a
+// running subtraction total turned a subtraction into one add but made every
+// accumulation dearer; on R-MAT 22 it was 15% slower overall.)
 // ---------------------------------------------------------------------------
 template <int K, typename VT>
 struct Sketch {
     uint32_t key[K];
     VT t[K];
-    VT D;
     bool lossy;
 
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int p = 0; p < K; ++p) { key[p] = kEmpty; t[p] = 0; }
-        D = 0;
         lossy = false;
     }
 
-    __device__ __forceinline__ VT value(int p) const { return t[p] > D ? t[p] - D : (VT)0; }
+    __device__ __forceinline__ VT value(int p) const { return t[p]; }
 
     __device__ __forceinline__ void update(uint32_t c, VT w, bool uncond) {
         bool has = false;
 #pragma unroll
         for (int p = 0; p < K; ++p) {
             const bool m = key[p] == c;
-            const VT up = (t[p] > D ? t[p] : D) + w;
-            t[p] = m ? up : t[p];
+            t[p] += m ? w : (VT)0;
             has |= m;
         }
         if (!has) {
-            if (uncond) { D += w; lossy = true; }
+            if (uncond) {
+#pragma unroll
+                for (int p = 0; p < K; ++p) t[p] = t[p] > w ? t[p] - w : (VT)0;
+                lossy = true;
+            }
             int e = -1;
 #pragma unroll
             for (int p = 0; p < K; ++p)
-                if (t[p] <= D) e = p;
+                if (t[p] == 0) e = p;
             if (e >= 0) {
-                const VT nt = D + w;
 #pragma unroll
                 for (int p = 0; p < K; ++p)
-                    if (p == e) { key[p] = c; t[p] = nt; }
+                    if (p == e) { key[p] = c; t[p] = w; }
             } else if (!uncond) {
-                D += w;
+#pragma unroll
+                for (int p = 0; p < K; ++p) t[p] = t[p] > w ? t[p] - w : (VT)0;
                 lossy = true;
             }
         }
@@ -133,17 +129,13 @@ __device__ __forceinline__ Chunk load_chunk(const SweepArgs& a, int64_t ch) {
 
 // Scans the chunks first, first + step, ... < c1 of the row [start, end) and
 // calls f(label of col, w) for entries inside the row that are not self-loops
-// (in refine mode only for neighbours inside the vertex's bound).  The next
-// chunk's loads are issued before the current chunk is processed.
+// (in refine mode only for neighbours inside the vertex's bound), in order.
+// One copy of f per chunk: the entries are shifted through slot 0.
 template <typename F>
 __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, int64_t c1, int step,
                                             int64_t start, int64_t end, uint32_t i, uint32_t bi, F&& f) {
-    if (first >= c1) return;
-    Chunk cur = load_chunk(a, first);
     for (int64_t ch = first; ch < c1; ch += step) {
-        Chunk nxt;
-        const bool more = ch + step < c1;
-        if (more) nxt = load_chunk(a, ch + step);
+        Chunk cur = load_chunk(a, ch);
         const int64_t e0 = ch * 4;
         uint32_t labs[4];
         bool ok[4];
@@ -161,10 +153,13 @@ __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, i
             for (int u = 0; u < 4; ++u)
                 if (ok[u]) ok[u] = __ldg(a.bound + cur.c[u]) == bi;
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (ok[u]) f(labs[u], cur.w[u]);
-        if (more) cur = nxt;
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            if (ok[0]) f(labs[0], cur.w[0]);
+            ok[0] = ok[1]; ok[1] = ok[2]; ok[2] = ok[3];
+            labs[0] = labs[1]; labs[1] = labs[2]; labs[2] = labs[3];
+            cur.w[0] = cur.w[1]; cur.w[1] = cur.w[2]; cur.w[2] = cur.w[3];
+        }
     }
 }
 
@@ -252,7 +247,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
     if (act) {
         if (G == 1) {
-            for_row(a, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
         } else {
             scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
         }
@@ -286,7 +281,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
                 for (int p = 0; p < K; ++p) acc[p] += c == cand[p] ? (VT)w : (VT)0;
             };
             if (G == 1) {
-                for_row(a, start, end, i, bi, add);
+                scan_chunks(a, first, c1, G, start, end, i, bi, add);
             } else {
                 scan_chunks(a, first, c1, G, start, end, i, bi, add);
             }
