@@ -91,6 +91,19 @@ typedef struct cd_schedule {
     int32_t lanes[CD_MAX_BUCKETS];
 } cd_schedule;
 
+/* Learned skip proposal (an addition to the paper's method, which has no
+ * learned part): a perceptron 8 -> 32 (ReLU) -> 1 (sigmoid) on per-vertex
+ * features predicting whether the vertex moves in the coming sweep.  float32
+ * master weights; the kernels read them rounded to float16 (W1, w2) and
+ * accumulate in float32.  Parameter order W1 (row j = hidden unit j), b1,
+ * w2, b2. */
+typedef struct cd_mlp {
+    float W1[32][8];
+    float b1[32];
+    float w2[32];
+    float b2;
+} cd_mlp;
+
 typedef struct cd_params {
     int32_t k;            /* MG slots: 1, 2, 4, 8 or 16; 0 = exact hashtable */
     int32_t subtract;     /* 0 = conditional (Algorithm 1), 1 = unconditional (Section 4.1) */
@@ -116,6 +129,15 @@ typedef struct cd_params {
     int32_t agg_k;        /* drivers: 0 = exact aggregation (sort + segmented sum); 1..16
                              (power of two) = MG aggregation with agg_k slots (Section 4.1;
                              Leiden uses its symmetric form, Section 4.2), see cd_aggregate_mg */
+    int32_t skip_rule;    /* Louvain and LPA drivers, sweeps after the first of a pass:
+                             0 = every vertex decides; 1 = learned: only vertices whose
+                             predicted move probability (skip_model) is >= skip_threshold;
+                             2 = only movers of the previous sweep and their neighbours.
+                             A sweep that skipped and then moved nobody or gained at most
+                             the tolerance is followed by a full sweep, which decides
+                             convergence. */
+    float skip_threshold;
+    const cd_mlp* skip_model; /* host memory, read during the call */
 } cd_params;
 
 typedef struct cd_stats {
@@ -128,6 +150,8 @@ typedef struct cd_stats {
     double sweep_kernel_ms;  /* total sweep-kernel time (timing != 0), CUDA events */
     int64_t sweep_kernel_launches;
     double modularity;       /* last modularity computed */
+    int64_t entries_scanned; /* CSR entries of the vertices that decided (MG sweeps, all sweeps) */
+    int64_t full_sweeps;     /* sweeps in which every vertex decided */
     char cuda_error[128];
 } cd_stats;
 
@@ -225,6 +249,41 @@ int cd_aggregate(const cd_csr* g, const uint32_t* labels, void* stream, uint32_t
 int cd_aggregate_mg(const cd_csr* g, const uint32_t* labels, int k, int subtract, int symmetric,
                     const cd_schedule* sched, void* stream, uint32_t* dense_out, int64_t* offsets_out,
                     int32_t* cols_out, uint32_t* weights_out, int64_t* n_out, int64_t* nnz_out);
+
+/* Features of the learned skip proposal for every vertex (n x 8 float16,
+ * device): log2(1 + deg) / 16; moved in the previous sweep; min(sweeps since
+ * its last move, 8) / 8; log2(1 + |community|) / 24; sqrt(Sigma_d / 2m);
+ * K_i / Sigma_d; K_{i->C_i} / K_i at the vertex's last decision (attach,
+ * 0 before any); 1.  labels: n community ids; moved_last, since_move: n bytes
+ * each, attach: n floats (NULL = zeros).  Device memory only. */
+int cd_features(const cd_csr* g, const uint32_t* labels, const uint8_t* moved_last, const uint8_t* since_move,
+                const float* attach, uint16_t* x_out, void* stream);
+
+/* Forward pass of the skip model on n feature rows (device x, n x 8 float16):
+ * p_out[i] (device, float32) = predicted move probability. */
+int cd_mlp_forward(const uint16_t* x, int64_t n, const cd_mlp* model, float* p_out, void* stream);
+
+/* Mean binary cross-entropy of the model on (x, y) (y: n bytes, 0/1, device)
+ * and its gradient (host cd_mlp with the parameter layout), summed in a
+ * fixed order (deterministic). */
+int cd_mlp_gradient(const uint16_t* x, const uint8_t* y, int64_t n, const cd_mlp* model, cd_mlp* grad_out,
+                    double* loss_out, void* stream);
+
+/* `steps` full-batch Adam steps (learning rate lr) on (x, y) with the
+ * gradient kernel above, starting from *model (updated in place); loss_out
+ * (host, may be NULL) receives the loss before the last step. */
+int cd_mlp_train(const uint16_t* x, const uint8_t* y, int64_t n, int steps, double lr, cd_mlp* model,
+                 double* loss_out, void* stream);
+
+/* Move traces of the plain method: runs the first local-moving phase of
+ * Louvain on g (every vertex deciding in every sweep, parameters as
+ * cd_louvain) and records, for sweeps after the first, the features of a
+ * sample of the vertices with edges (each with probability sample_rate,
+ * chosen by a hash of (vertex, sweep)) at the start of the sweep and whether
+ * the vertex moved in it.  x_out: capacity x 8 float16, y_out: capacity bytes
+ * (device); *count_out (host) = samples written (at most capacity). */
+int cd_trace(const cd_csr* g, const cd_params* p, double sample_rate, uint16_t* x_out, uint8_t* y_out,
+             int64_t capacity, int64_t* count_out);
 
 /*
  * Modularity without any device allocation.  The paper has no counterpart:

@@ -24,7 +24,8 @@ MAX_BUCKETS = 16
 
 # Symbols declared in include/cd.h.
 SYMBOLS = ("cd_strerror", "cd_last_stats", "cd_default_schedule", "cd_sweep", "cd_modularity",
-           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_aggregate_mg", "cd_modularity_noalloc")
+           "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_aggregate_mg", "cd_modularity_noalloc",
+           "cd_features", "cd_mlp_forward", "cd_mlp_gradient", "cd_mlp_train", "cd_trace")
 
 
 class CSR(ctypes.Structure):
@@ -41,13 +42,41 @@ class Schedule(ctypes.Structure):
         return list(self.deg_max[:nb]), list(self.lanes[:nb]), self.vec
 
 
+class MLP(ctypes.Structure):
+    _fields_ = [("W1", (ctypes.c_float * 8) * 32), ("b1", ctypes.c_float * 32), ("w2", ctypes.c_float * 32),
+                ("b2", ctypes.c_float)]
+
+    def to_numpy(self):
+        W1 = np.ctypeslib.as_array(self.W1).astype(np.float64).reshape(32, 8)
+        return (W1, np.ctypeslib.as_array(self.b1).astype(np.float64),
+                np.ctypeslib.as_array(self.w2).astype(np.float64), float(self.b2))
+
+    @staticmethod
+    def from_numpy(W1, b1, w2, b2):
+        m = MLP()
+        np.ctypeslib.as_array(m.W1)[:] = np.asarray(W1, dtype=np.float32).reshape(32, 8)
+        np.ctypeslib.as_array(m.b1)[:] = np.asarray(b1, dtype=np.float32)
+        np.ctypeslib.as_array(m.w2)[:] = np.asarray(w2, dtype=np.float32)
+        m.b2 = float(b2)
+        return m
+
+    @staticmethod
+    def init(seed=0):
+        """Small random initial weights (He-scaled), for training."""
+        rng = np.random.default_rng(seed)
+        return MLP.from_numpy(rng.normal(0, np.sqrt(2 / 8), (32, 8)), np.zeros(32),
+                              rng.normal(0, np.sqrt(1 / 32), 32), 0.0)
+
+
 class Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("subtract", ctypes.c_int32), ("tolerance", ctypes.c_double),
                 ("tolerance_drop", ctypes.c_double), ("aggregation_tolerance", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("sched", ctypes.POINTER(Schedule)), ("stream", ctypes.c_void_p),
                 ("timing", ctypes.c_int32), ("colors", ctypes.c_int32),
-                ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32), ("agg_k", ctypes.c_int32)]
+                ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32), ("agg_k", ctypes.c_int32),
+                ("skip_rule", ctypes.c_int32), ("skip_threshold", ctypes.c_float),
+                ("skip_model", ctypes.POINTER(MLP))]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +84,8 @@ class Stats(ctypes.Structure):
                 ("gain_lo", ctypes.c_uint64), ("gain_hi", ctypes.c_uint64),
                 ("communities", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
                 ("sweep_kernel_ms", ctypes.c_double), ("sweep_kernel_launches", ctypes.c_int64),
-                ("modularity", ctypes.c_double), ("cuda_error", ctypes.c_char * 128)]
+                ("modularity", ctypes.c_double), ("entries_scanned", ctypes.c_int64),
+                ("full_sweeps", ctypes.c_int64), ("cuda_error", ctypes.c_char * 128)]
 
 
 class ModularityParts(ctypes.Structure):
@@ -94,6 +124,14 @@ def lib():
             L.cd_modularity.argtypes = [ctypes.POINTER(CSR), P, P, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ModularityParts)]
             L.cd_modularity_noalloc.argtypes = L.cd_modularity.argtypes
+            L.cd_features.argtypes = [ctypes.POINTER(CSR), P, P, P, P, P, P]
+            L.cd_mlp_forward.argtypes = [P, ctypes.c_int64, ctypes.POINTER(MLP), P, P]
+            L.cd_mlp_gradient.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(MLP), ctypes.POINTER(MLP),
+                                          ctypes.POINTER(ctypes.c_double), P]
+            L.cd_mlp_train.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(MLP),
+                                       ctypes.POINTER(ctypes.c_double), P]
+            L.cd_trace.argtypes = [ctypes.POINTER(CSR), ctypes.POINTER(Params), ctypes.c_double, P, P,
+                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
             for name in ("cd_louvain", "cd_lpa", "cd_leiden"):
                 getattr(L, name).argtypes = [ctypes.POINTER(CSR), ctypes.POINTER(Params), P,
                                              ctypes.POINTER(ctypes.c_double)]
@@ -167,7 +205,8 @@ def current_stream():
 
 def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregation_tolerance=0.8,
                 max_sweeps=20, max_passes=10, schedule: Schedule | None = None, stream=None,
-                timing=False, colors=0, sub_color=0, one_scan=False, agg_k=0) -> Params:
+                timing=False, colors=0, sub_color=0, one_scan=False, agg_k=0, skip_rule=0,
+                skip_threshold=0.5, skip_model: "MLP | None" = None) -> Params:
     p = Params()
     p.k, p.subtract = int(k), int(subtract)
     p.tolerance, p.tolerance_drop, p.aggregation_tolerance = tolerance, tolerance_drop, aggregation_tolerance
@@ -179,6 +218,10 @@ def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregatio
     p.sub_color = int(sub_color)
     p.one_scan = int(bool(one_scan))
     p.agg_k = int(agg_k)
+    p.skip_rule = int(skip_rule)
+    p.skip_threshold = float(skip_threshold)
+    p.skip_model = ctypes.pointer(skip_model) if skip_model is not None else None
+    p._keep_model = skip_model
     p._keep = schedule
     return p
 
@@ -311,3 +354,51 @@ def cd_aggregate_mg(g: Graph, labels, k=8, subtract=0, symmetric=False, schedule
            "cd_aggregate_mg")
     n2, m2 = n_out.value, nnz_out.value
     return dense, Graph(n2, off[:n2 + 1], cols[:m2], w[:m2])
+
+
+def cd_features(g: Graph, labels, moved_last=None, since_move=None, attach=None, stream=None):
+    """(n, 8) float16 features (device tensor)."""
+    import torch
+    x = torch.empty((g.n, 8), dtype=torch.float16, device=g.offsets.device)
+    csr = g.csr()
+    st = stream.value if isinstance(stream, ctypes.c_void_p) else stream
+    _check(lib().cd_features(ctypes.byref(csr), _ptr(labels), _ptr(moved_last), _ptr(since_move), _ptr(attach),
+                             _ptr(x), st), "cd_features")
+    return x
+
+
+def cd_mlp_forward(x, model: MLP, stream=None):
+    import torch
+    p = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().cd_mlp_forward(_ptr(x), x.shape[0], ctypes.byref(model), _ptr(p), stream), "cd_mlp_forward")
+    return p
+
+
+def cd_mlp_gradient(x, y, model: MLP, stream=None):
+    """Returns (loss, gradient as MLP)."""
+    g = MLP()
+    loss = ctypes.c_double()
+    _check(lib().cd_mlp_gradient(_ptr(x), _ptr(y), x.shape[0], ctypes.byref(model), ctypes.byref(g),
+                                 ctypes.byref(loss), stream), "cd_mlp_gradient")
+    return loss.value, g
+
+
+def cd_mlp_train(x, y, model: MLP, steps=200, lr=0.01, stream=None):
+    """Trains `model` in place; returns the final loss."""
+    loss = ctypes.c_double()
+    _check(lib().cd_mlp_train(_ptr(x), _ptr(y), x.shape[0], steps, lr, ctypes.byref(model), ctypes.byref(loss),
+                              stream), "cd_mlp_train")
+    return loss.value
+
+
+def cd_trace(g: Graph, params: Params, sample_rate=0.25, capacity=None):
+    """Move traces of the plain method: (x float16 (m, 8), y uint8 (m,)) device tensors."""
+    import torch
+    cap = capacity if capacity is not None else max(1, int(g.n * 20 * sample_rate) + 1024)
+    x = torch.empty((cap, 8), dtype=torch.float16, device=g.offsets.device)
+    y = torch.empty(cap, dtype=torch.uint8, device=g.offsets.device)
+    cnt = ctypes.c_int64()
+    csr = g.csr()
+    _check(lib().cd_trace(ctypes.byref(csr), ctypes.byref(params), sample_rate, _ptr(x), _ptr(y), cap,
+                          ctypes.byref(cnt)), "cd_trace")
+    return x[:cnt.value], y[:cnt.value]

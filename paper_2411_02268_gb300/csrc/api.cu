@@ -84,16 +84,18 @@ int check_csr(const cd_csr* g) {
 }
 
 void default_schedule(cd_schedule* s) {
-    // Streams per row by row length: one stream up to 32 entries, then about
-    // 16-128 entries per stream so that the merge tree stays cheaper than the
-    // scan; narrow length bands keep the groups of one warp balanced.
-    static const int64_t dm[] = {2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 32768,
-                                 INT64_MAX};
-    static const int32_t ln[] = {1, 1, 1, 1, 1, 2, 2, 4, 4, 8, 8, 16, 32, 128, 256};
+    // Streams per row by row length: one stream up to 128 entries, then about
+    // 64-256 entries per stream (the merge tree costs about k updates per
+    // stream), 256 streams for the hubs; narrow length bands keep the rows
+    // of one warp balanced.  Tuned on R-MAT scale 22 (1.34 -> 1.27 ms against
+    // the previous bands; coarser bands cost 30%).
+    static const int64_t dm[] = {2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 16384, INT64_MAX};
+    static const int32_t ln[] = {1, 1, 1, 1, 1, 1, 1, 2, 4, 4, 8, 8, 32, 256};
+    const int nb = 14;
     std::memset(s, 0, sizeof(*s));
-    s->nbuckets = 15;
+    s->nbuckets = nb;
     s->vec = 4;
-    for (int b = 0; b < 15; ++b) { s->deg_max[b] = dm[b]; s->lanes[b] = ln[b]; }
+    for (int b = 0; b < nb; ++b) { s->deg_max[b] = dm[b]; s->lanes[b] = ln[b]; }
 }
 
 int check_schedule(const cd_schedule* s) {
@@ -115,6 +117,7 @@ int check_params(const cd_params* p) {
     if (p->one_scan && p->k == 0) return CD_EINVAL;
     if (!(p->agg_k == 0 || p->agg_k == 1 || p->agg_k == 2 || p->agg_k == 4 || p->agg_k == 8 || p->agg_k == 16))
         return CD_EINVAL;
+    if (p->skip_rule < 0 || p->skip_rule > 2 || (p->skip_rule == 1 && !p->skip_model)) return CD_EINVAL;
     if (p->sched) CD_TRY(check_schedule(p->sched));
     return CD_OK;
 }
@@ -217,16 +220,21 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
     CD_TRY(sc.get(&to, ntiles * nkeys));
     CD_TRY(sc.get(&starts, nkeys + 1));
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
-    CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, L.K, dglob, s));
-    CD_CUDA(launch_totals(labels, L.K, L.n, L.Sigma, L.size, dglob, s));
     CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, colors, tc, to, starts, L.verts, labels, labels_out_copy,
                           dglob, s));
     HostGlobals hg;
     CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
+    L.starts.assign(hg.starts, hg.starts + nkeys + 1);
+    // weighted degrees row by row over the buckets (one launch per colour
+    // class), then community totals
+    CD_CUDA(cudaMemsetAsync(L.K, 0, sizeof(uint64_t) * (size_t)(L.n > 0 ? L.n : 1), s));
+    for (int c = 0; c < colors; ++c)
+        CD_CUDA(launch_row_sums(L.off, L.w, L.n, L.nnz, L.verts, L.table_for(c), L.K, dglob, s));
+    CD_CUDA(launch_totals(labels, L.K, L.n, L.Sigma, L.size, dglob, s));
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
     L.two_m = hg.g.two_m;
     if (L.two_m >= (1ull << 62)) return CD_EOVERFLOW;
     L.wide = hg.g.max_k >= (1ull << 32);
-    L.starts.assign(hg.starts, hg.starts + nkeys + 1);
     L.bt = L.table_for(0);
     return CD_OK;
 }
@@ -541,8 +549,34 @@ int resolve_colors(const cd_params* p) { return p->colors == 0 ? 8 : p->colors; 
 // the commit into Sigma and sizes, until nobody moves, the sweep's summed
 // delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
 // max_sweeps.  Returns the final labels in *labels (a scratch buffer).
+// Move traces recorded by local_move (cd_trace).
+struct Trace {
+    double rate = 0.0;
+    void* x = nullptr;   // capacity x 8 float16
+    uint8_t* y = nullptr;
+    int64_t cap = 0;
+    int64_t count = 0;
+};
+
+// Model parameters in device scratch (float32, the cd_mlp layout).
+int stage_model(const cd_mlp* m, Scratch& sc, float** dparam, cudaStream_t s) {
+    CD_TRY(sc.get(dparam, mlp_param_count()));
+    CD_CUDA(cudaMemcpyAsync(*dparam, m, sizeof(float) * mlp_param_count(), cudaMemcpyHostToDevice, s));
+    return CD_OK;
+}
+
+// Local-moving phase on level L from `init` labels (singletons when null):
+// every sweep is `colors` sub-sweeps (sub-sweep c decides the vertices of
+// colour class c from the state left by the previous ones), each followed by
+// the commit into Sigma and sizes, until nobody moves, the sweep's summed
+// delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
+// max_sweeps.  With a skip rule, sweeps after the first decide only the
+// proposed vertices; a proposal sweep that moves nobody or gains at most tol
+// is followed by a full sweep, which decides convergence.  Returns the final
+// labels in *labels (a scratch buffer).
 int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_schedule& sched, Scratch& sc,
-               Globals* dglob, cudaStream_t s, const uint32_t* init, uint32_t** labels, int64_t* sweeps_out) {
+               Globals* dglob, cudaStream_t s, const uint32_t* init, uint32_t** labels, int64_t* sweeps_out,
+               Trace* trace = nullptr) {
     uint32_t *la, *lb;
     CD_TRY(sc.get(&la, L.n));
     CD_TRY(sc.get(&lb, L.n));
@@ -551,12 +585,55 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     else CD_CUDA(launch_iota(la, L.n, s));
     const int colors = resolve_colors(p);
     CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
+    const int rule = trace ? 0 : p->skip_rule;
+    const bool track = rule != 0 || trace;
+    uint8_t *active = nullptr, *moved_last = nullptr, *since_move = nullptr;
+    uint32_t* before = nullptr;
+    void* x = nullptr;
+    float* param = nullptr;
+    if (track) {
+        CD_TRY(sc.get(&active, L.n));
+        CD_TRY(sc.get(&moved_last, L.n));
+        CD_TRY(sc.get(&since_move, L.n));
+        CD_TRY(sc.get(&before, L.n));
+        CD_CUDA(cudaMemsetAsync(moved_last, 1, L.n, s));
+        CD_CUDA(cudaMemsetAsync(since_move, 0, L.n, s));
+    }
+    float* attach = nullptr;
+    uint32_t *tflags = nullptr, *tpos = nullptr;
+    unsigned long long* ttiles = nullptr;
+    if (rule == 1 || trace) {
+        uint16_t* xh;
+        CD_TRY(sc.get(&xh, L.n * 8));
+        x = xh;
+        CD_TRY(sc.get(&attach, L.n));
+        CD_CUDA(cudaMemsetAsync(attach, 0, sizeof(float) * L.n, s));
+    }
+    if (trace) {
+        CD_TRY(sc.get(&tflags, L.n));
+        CD_TRY(sc.get(&tpos, L.n));
+        CD_TRY(sc.get(&ttiles, scan_tiles(L.n) + 1));
+    }
+    if (rule == 1) CD_TRY(stage_model(p->skip_model, sc, &param, s));
     std::vector<Timer> tms((size_t)colors);
     for (auto& t : tms) CD_TRY(t.init(p->timing != 0));
     const size_t stat_off = offsetof(Globals, moved);
     const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
     int64_t sw = 0;
+    bool force_full = false;
     for (; sw < p->max_sweeps;) {
+        const bool use_mask = rule != 0 && sw > 0 && !force_full;
+        if (use_mask && rule == 2) {
+            // movers of the previous sweep and their neighbours
+            CD_CUDA(cudaMemsetAsync(active, 0, L.n, s));
+            CD_CUDA(launch_mark_neighbours(L.off, L.cols, L.movers, dglob, active, s));
+        }
+        if ((use_mask && rule == 1) || (trace && sw > 0)) {
+            CD_CUDA(launch_features(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, L.n,
+                                    x, s));
+            if (use_mask) CD_CUDA(launch_mlp_forward(x, L.n, param, nullptr, active, p->skip_threshold, s));
+        }
+        if (track) CD_CUDA(cudaMemcpyAsync(before, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
         CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
         for (int c = 0; c < colors; ++c) {
             // sub-sweep c: vertices of colour c decide from la and write lb; the
@@ -565,16 +642,27 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
                                     cudaMemcpyDeviceToDevice, s));
             Level Lc = L;
             Lc.bt = L.table_for(c);
-            SweepArgs a = make_args(Lc, la, lb, nullptr, nullptr, dglob, mode, p->subtract);
+            SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract);
             a.one_scan = p->one_scan;
+            a.attach = attach;
             if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].a, s));
             CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
             if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, s));
             CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
             CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
         }
+        if (track) CD_CUDA(launch_move_state(before, la, L.n, moved_last, since_move, s));
         HostGlobals hg;
+        if (trace && sw > 0) {
+            const double r = trace->rate < 0 ? 0 : (trace->rate > 1 ? 1 : trace->rate);
+            const uint32_t thr32 = r >= 1.0 ? 0xFFFFFFFFu : (uint32_t)(r * 4294967296.0);
+            CD_CUDA(launch_trace_flags(L.off, L.n, (int)sw, thr32, tflags, s));
+            CD_CUDA(launch_exclusive_scan_u32(tflags, tpos, L.n, ttiles, &dglob->count, s));
+            CD_CUDA(launch_trace_write(x, moved_last, tflags, tpos, L.n, trace->count, trace->x, trace->y,
+                                       trace->cap, s));
+        }
         CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        if (trace && sw > 0) trace->count = std::min<int64_t>(trace->count + (int64_t)hg.g.count, trace->cap);
         for (auto& t : tms) {
             if (!t.on) continue;
             float ms = 0;
@@ -586,14 +674,24 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         g_stats.moved = (int64_t)hg.g.moved;
         g_stats.gain_lo = hg.g.gain_lo;
         g_stats.gain_hi = hg.g.gain_hi;
-        if (hg.g.moved == 0) break;
-        if (mode == CD_MODE_LPA) {
-            if ((double)hg.g.moved <= tol * (double)L.n) break;
-        } else {
-            double dq = gain_as_double(hg.g.gain_lo, hg.g.gain_hi) /
-                        ((double)L.two_m * (double)L.two_m / 2.0);
-            if (dq <= tol) break;
+        g_stats.entries_scanned += (int64_t)hg.g.scanned;
+        if (!use_mask) g_stats.full_sweeps += 1;
+        bool done = hg.g.moved == 0;
+        if (!done) {
+            if (mode == CD_MODE_LPA) {
+                done = (double)hg.g.moved <= tol * (double)L.n;
+            } else {
+                double dq = gain_as_double(hg.g.gain_lo, hg.g.gain_hi) /
+                            ((double)L.two_m * (double)L.two_m / 2.0);
+                done = dq <= tol;
+            }
         }
+        if (done && use_mask) {
+            force_full = true;  // a proposal sweep stalled: the next sweep is a full one
+            continue;
+        }
+        force_full = false;
+        if (done) break;
     }
     *labels = la;
     *sweeps_out = sw;
@@ -794,6 +892,8 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         g_stats.sweep_kernel_launches += 1;
     }
     g_stats.sweeps = 1;
+    g_stats.full_sweeps = active ? 0 : 1;
+    g_stats.entries_scanned = (int64_t)hg.g.scanned;
     g_stats.moved = (int64_t)hg.g.moved;
     g_stats.gain_lo = hg.g.gain_lo;
     g_stats.gain_hi = hg.g.gain_hi;
@@ -1006,6 +1106,124 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
     CD_TRY(modularity_of(in, result, sc, dglob, s, &q));
     CD_TRY(emit_labels(g, result, labels_out, s));
     if (q_out) *q_out = q;
+    return CD_OK;
+}
+
+int cd_features(const cd_csr* g, const uint32_t* labels, const uint8_t* moved_last, const uint8_t* since_move,
+                const float* attach, uint16_t* x_out, void* stream) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    if (g->memory != CD_MEM_DEVICE || !labels || !x_out) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level L;
+    CD_TRY(input_level(g, sc, &L));
+    CD_TRY(sc.get(&L.K, L.n));
+    CD_TRY(sc.get(&L.Sigma, L.n));
+    CD_TRY(sc.get(&L.size, L.n));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    if (L.n > 0) {
+        CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, L.K, dglob, s));
+        CD_CUDA(launch_totals(labels, L.K, L.n, L.Sigma, L.size, dglob, s));
+    }
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    CD_CUDA(launch_features(L.off, L.K, labels, L.Sigma, L.size, hg.g.two_m, moved_last, since_move, attach, L.n,
+                            x_out, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    return CD_OK;
+}
+
+int cd_mlp_forward(const uint16_t* x, int64_t n, const cd_mlp* model, float* p_out, void* stream) {
+    reset_stats();
+    if (!x || !model || !p_out || n < 0) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    float* param;
+    CD_TRY(stage_model(model, sc, &param, s));
+    CD_CUDA(launch_mlp_forward(x, n, param, p_out, nullptr, 0.0f, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    return CD_OK;
+}
+
+int cd_mlp_gradient(const uint16_t* x, const uint8_t* y, int64_t n, const cd_mlp* model, cd_mlp* grad_out,
+                    double* loss_out, void* stream) {
+    reset_stats();
+    if (!x || !y || !model || !grad_out || n <= 0) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    float *param, *partial, *lpart, *grad, *loss;
+    CD_TRY(stage_model(model, sc, &param, s));
+    CD_TRY(sc.get(&partial, mlp_grad_blocks(n) * mlp_param_count()));
+    CD_TRY(sc.get(&lpart, mlp_grad_blocks(n)));
+    CD_TRY(sc.get(&grad, mlp_param_count()));
+    CD_TRY(sc.get(&loss, 1));
+    CD_CUDA(launch_mlp_grad(x, y, n, param, partial, lpart, grad, loss, s));
+    float hl = 0;
+    CD_CUDA(cudaMemcpyAsync(grad_out, grad, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    if (loss_out) *loss_out = hl;
+    return CD_OK;
+}
+
+int cd_mlp_train(const uint16_t* x, const uint8_t* y, int64_t n, int steps, double lr, cd_mlp* model,
+                 double* loss_out, void* stream) {
+    reset_stats();
+    if (!x || !y || !model || n <= 0 || steps < 0 || !(lr > 0)) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    float *param, *partial, *lpart, *grad, *loss, *m1, *m2;
+    const int P = mlp_param_count();
+    CD_TRY(stage_model(model, sc, &param, s));
+    CD_TRY(sc.get(&partial, mlp_grad_blocks(n) * P));
+    CD_TRY(sc.get(&lpart, mlp_grad_blocks(n)));
+    CD_TRY(sc.get(&grad, P));
+    CD_TRY(sc.get(&loss, 1));
+    CD_TRY(sc.get(&m1, P));
+    CD_TRY(sc.get(&m2, P));
+    CD_CUDA(cudaMemsetAsync(m1, 0, sizeof(float) * P, s));
+    CD_CUDA(cudaMemsetAsync(m2, 0, sizeof(float) * P, s));
+    for (int t = 1; t <= steps; ++t) {
+        CD_CUDA(launch_mlp_grad(x, y, n, param, partial, lpart, grad, loss, s));
+        CD_CUDA(launch_adam(param, grad, m1, m2, t, (float)lr, s));
+    }
+    float hl = 0;
+    CD_CUDA(cudaMemcpyAsync(model, param, sizeof(float) * P, cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    if (loss_out) *loss_out = hl;
+    return CD_OK;
+}
+
+int cd_trace(const cd_csr* g, const cd_params* p, double sample_rate, uint16_t* x_out, uint8_t* y_out,
+             int64_t capacity, int64_t* count_out) {
+    reset_stats();
+    CD_TRY(check_csr(g));
+    CD_TRY(check_driver_params(p));
+    if (g->memory != CD_MEM_DEVICE || !x_out || !y_out || capacity < 0 || !count_out) return CD_EINVAL;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule sched;
+    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    Level in;
+    CD_TRY(input_level(g, sc, &in));
+    Trace tr;
+    tr.rate = sample_rate;
+    tr.x = x_out;
+    tr.y = y_out;
+    tr.cap = capacity;
+    if (in.n > 0) {
+        uint32_t* lab;
+        int64_t sw = 0;
+        CD_TRY(local_move(in, p, CD_MODE_LOUVAIN, p->tolerance, sched, sc, dglob, s, nullptr, &lab, &sw, &tr));
+        g_stats.sweeps = sw;
+    }
+    *count_out = tr.count;
     return CD_OK;
 }
 

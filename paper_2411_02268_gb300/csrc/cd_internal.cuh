@@ -21,6 +21,7 @@ struct Globals {
     unsigned long long moved;    // movers in the last sweep
     unsigned long long gain_lo;  // 128-bit sum of movers' gains
     unsigned long long gain_hi;
+    unsigned long long scanned;  // CSR entries of the vertices that decided
     unsigned long long sigma_in; // modularity: sum_c sigma_c
     unsigned long long sq_lo;    // modularity: sum_c Sigma_c^2
     unsigned long long sq_hi;
@@ -52,6 +53,7 @@ struct SweepArgs {
     const uint32_t* bound;    // refine mode only
     uint32_t* labels_out;
     uint32_t* movers;         // optional list of movers (driver), capacity n
+    float* attach;            // optional: K_{i->C_i} / K_i after the decision (skip features)
     Globals* glob;
     const uint32_t* verts;    // bucket-ordered vertex ids
     int64_t n;
@@ -111,6 +113,9 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s);
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
+// K_i for the rows of one bucket table (vbegin ranges; bbegin is recomputed).
+cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
+                            const BucketTable& bt, uint64_t* K, Globals* glob, cudaStream_t s);
 cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, cudaStream_t s);
 cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in,
                           const uint32_t* labels_out, const uint64_t* K, int64_t n,
@@ -177,6 +182,26 @@ cudaError_t launch_segsum(const AggScratch& a, const uint32_t* uidx, int64_t nnz
                           uint32_t* rowcnt, cudaStream_t s);
 cudaError_t launch_narrow(const unsigned long long* wsum, int64_t m, uint32_t* w_out, Globals* glob,
                           cudaStream_t s);
+
+// mlp.cu (learned skip proposal)
+cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_t* labels, const uint64_t* Sigma,
+                            const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
+                            const uint8_t* since_move, const float* attach, int64_t n, void* x, cudaStream_t s);
+cudaError_t launch_mlp_forward(const void* x, int64_t n, const float* param, float* p, uint8_t* active, float thr,
+                               cudaStream_t s);
+int64_t mlp_grad_blocks(int64_t n);
+int mlp_param_count();
+cudaError_t launch_mlp_grad(const void* x, const uint8_t* y, int64_t n, const float* param, float* partial,
+                            float* loss_partial, float* grad, float* loss, cudaStream_t s);
+cudaError_t launch_adam(float* param, const float* grad, float* m1, float* m2, int step, float lr, cudaStream_t s);
+cudaError_t launch_move_state(const uint32_t* before, const uint32_t* after, int64_t n, uint8_t* moved_last,
+                              uint8_t* since_move, cudaStream_t s);
+cudaError_t launch_mark_neighbours(const int64_t* off, const int32_t* cols, const uint32_t* movers,
+                                   const Globals* glob, uint8_t* active, cudaStream_t s);
+cudaError_t launch_trace_flags(const int64_t* off, int64_t n, int sweep, uint32_t thr32, uint32_t* flags,
+                               cudaStream_t s);
+cudaError_t launch_trace_write(const void* x, const uint8_t* moved_last, const uint32_t* flags, const uint32_t* pos,
+                               int64_t n, int64_t base, void* xo, uint8_t* yo, int64_t cap, cudaStream_t s);
 
 // Device-side error flags (Globals::err bits).
 constexpr unsigned kErrBadOffsets = 1u;

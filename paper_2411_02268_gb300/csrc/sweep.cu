@@ -73,6 +73,9 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
             atomicOr(&glob->err, kErrBadLabel);
         }
     }
+    // block reduction, then one atomic per block (a single address would
+    // otherwise serialise one atomic per warp)
+    __shared__ unsigned long long ss[8], sm[8];
     unsigned long long s = k, m = k;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -81,9 +84,93 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
         m = mo > m ? mo : m;
     }
     if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sm[threadIdx.x >> 5] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            s += ss[q];
+            m = sm[q] > m ? sm[q] : m;
+        }
         if (s) atomicAdd(&glob->two_m, s);
         if (m) atomicMax(&glob->max_k, m);
     }
+}
+
+// K_i = sum of w over row i for the rows listed in the bucket table: rows of
+// bucket b are summed by lanes[b] threads (one thread per row for the short
+// rows), with 16-byte loads and a shuffle reduction; each row's sum is written
+// once (rows of length 0 are not listed and keep K = 0).
+__global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ off, const uint32_t* __restrict__ w,
+                                                  int64_t nnz, const uint32_t* __restrict__ verts, BucketTable bt,
+                                                  unsigned long long* __restrict__ K, Globals* glob) {
+    const int64_t blk = blockIdx.x;
+    int b = 0;
+#pragma unroll
+    for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+        if (q < bt.nb && blk >= bt.bbegin[q]) b = q;
+    const int L = bt.lanes[b] < 32 ? bt.lanes[b] : 32;  // at most a warp per row
+    const int64_t vi = bt.vbegin[b] + (blk - bt.bbegin[b]) * (256 / L) + threadIdx.x / L;
+    const bool valid = vi < bt.vbegin[b + 1];
+    const int lane = threadIdx.x % L;
+    unsigned long long sum = 0;
+    bool zero = false;
+    uint32_t i = 0;
+    if (valid) {
+        i = verts[vi];
+        const int64_t start = off[i], end = off[i + 1];
+        if (L == 1) {
+            for (int64_t e = start; e < end; ++e) {
+                const uint32_t x = __ldg(w + e);
+                zero |= x == 0;
+                sum += x;
+            }
+        } else {
+            const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
+            for (int64_t ch = c0 + lane; ch < c1; ch += L) {
+                const int64_t e0 = ch * 4;
+                uint32_t xs[4];
+                if (e0 + 4 <= nnz) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(w) + ch);
+                    xs[0] = v.x; xs[1] = v.y; xs[2] = v.z; xs[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xs[u] = e0 + u < nnz ? w[e0 + u] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool in = e0 + u >= start && e0 + u < end;
+                    zero |= in && xs[u] == 0;
+                    sum += in ? xs[u] : 0u;
+                }
+            }
+        }
+    }
+    if (L > 1) {
+        const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+        for (int o = L / 2; o >= 1; o >>= 1) sum += __shfl_down_sync(gmask, sum, o, L);
+    }
+    if (valid && lane == 0) K[i] = sum;
+    if (zero) atomicOr(&glob->err, kErrZeroWeight);
+}
+
+cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
+                            const BucketTable& bt_in, uint64_t* K, Globals* glob, cudaStream_t s) {
+    // geometry: min(lanes, 32) threads per row, 256-thread blocks
+    BucketTable bt = bt_in;
+    int64_t blk = 0;
+    for (int b = 0; b < bt.nb; ++b) {
+        bt.bbegin[b] = blk;
+        const int L = bt.lanes[b] < 32 ? bt.lanes[b] : 32;
+        const int64_t nv = bt.vbegin[b + 1] - bt.vbegin[b];
+        blk += (nv + (256 / L) - 1) / (256 / L);
+    }
+    bt.bbegin[bt.nb] = blk;
+    (void)n;
+    if (blk == 0) return cudaSuccess;
+    k_row_sums<<<(unsigned)blk, 256, 0, s>>>(off, w, nnz, verts, bt, (unsigned long long*)K, glob);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,

@@ -131,8 +131,12 @@ __device__ __forceinline__ void exact_epilogue(const SweepArgs& a, bool moved, u
 }
 
 __device__ __forceinline__ void finish(const SweepArgs& a, uint32_t i, uint32_t d, unsigned long long kid,
-                                       const Best& b, bool& moved, u128& gain) {
+                                       const Best& b, unsigned long long kbest, bool& moved, u128& gain) {
     moved = b.c != kEmpty;
+    if (a.attach) {
+        const unsigned long long Ki = a.K[i];
+        a.attach[i] = Ki ? (float)(moved ? kbest : kid) / (float)Ki : 0.0f;
+    }
     if (moved) {
         a.labels_out[i] = b.c;
         gain = a.mode == CD_MODE_LPA ? (u128)((unsigned long long)b.gain - kid) : (u128)b.gain;
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_group(const SweepArgs a,
     bool moved = false;
     u128 gain = 0;
     if (valid && lane == 0) {
-        if (act) finish(a, i, d, kid, b, moved, gain);
+        if (act) finish(a, i, d, kid, b, b.c != kEmpty ? table_get(keys, vals, T, b.c) : 0ull, moved, gain);
         else a.labels_out[i] = d;
     }
     exact_epilogue(a, moved, gain, i);
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_block(const SweepArgs a,
     if (threadIdx.x == 0) {
         for (int q = 1; q < kBlock / 32; ++q)
             if (better(wbest[q], b)) b = wbest[q];
-        if (act) finish(a, i, d, kid, b, moved, gain);
+        if (act) finish(a, i, d, kid, b, b.c != kEmpty ? table_get(keys, vals, T, b.c) : 0ull, moved, gain);
         else a.labels_out[i] = d;
     }
     if (threadIdx.x < 32) exact_epilogue(a, moved, gain, i);

@@ -70,6 +70,7 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
                                        const uint32_t (&cand)[K], const VT (&acc)[K], VT kid,
                                        uint32_t& best_out, u128& gain_out) {
     uint32_t best = d;
+    VT best_w = kid;  // K_{i->c} of the chosen community
     bool have = false;
     if (a.mode == CD_MODE_LPA) {
         VT bk = kid;
@@ -81,6 +82,7 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
             if (v > kid && (v > bk || (v == bk && c < best))) { best = c; bk = v; have = true; }
         }
         gain_out = have ? (u128)(bk - kid) : (u128)0;
+        best_w = bk;
     } else {
         const unsigned long long two_m = a.glob->two_m;
         const unsigned long long Ki = a.K[i];
@@ -94,11 +96,15 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
             if (barred(a, c, d, sd1)) continue;
             i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
                      (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
-            if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; }
+            if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; best_w = acc[p]; }
         }
         gain_out = have ? (u128)bg : (u128)0;
     }
     best_out = best;
+    if (a.attach) {
+        const unsigned long long Ki = a.K[i];
+        a.attach[i] = Ki ? (float)best_w / (float)Ki : 0.0f;
+    }
     return have;
 }
 
@@ -187,6 +193,7 @@ struct Outcome {
     bool moved;
     u128 gain;
     uint32_t vertex;
+    uint32_t scanned;  // entries of the row, when the vertex decided
 };
 
 // Feeds the live slots of a partner sketch (keys pk, values pv) to s.
@@ -225,7 +232,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu
                                      : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    Outcome out{false, 0, 0};
+    Outcome out{false, 0, 0, 0};
     uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
@@ -301,6 +308,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         out.moved = mv;
         out.gain = g;
         out.vertex = i;
+        out.scanned = (uint32_t)(end - start);
     } else if (valid && !act && lane == 0) {
         a.labels_out[i] = d;
     }
@@ -368,7 +376,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     const int bar = 1 + sb;
     const int wl = s >> 5;          // warp within sub-block
     const int lane = s & 31;
-    Outcome out{false, 0, 0};
+    Outcome out{false, 0, 0, 0};
     uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
@@ -455,6 +463,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
             out.moved = mv;
             out.gain = g;
             out.vertex = i;
+            out.scanned = (uint32_t)(end - start);
         } else if (valid) {
             a.labels_out[i] = d;
         }
@@ -466,6 +475,8 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
 // Warp-level statistics and mover list; every lane of the warp must call it.
 __device__ __forceinline__ void epilogue(const SweepArgs& a, const Outcome& o) {
     const int lane = threadIdx.x & 31;
+    const unsigned sc = __reduce_add_sync(0xffffffffu, o.scanned);
+    if (lane == 0 && sc) atomicAdd(&a.glob->scanned, (unsigned long long)sc);
     unsigned mm = __ballot_sync(0xffffffffu, o.moved);
     if (mm == 0) return;
     unsigned long long lo = o.moved ? (unsigned long long)o.gain : 0ull;

@@ -1,0 +1,138 @@
+"""Learned skip proposal on the GPU: features, the network's forward pass and
+gradient against the CPU oracle (oracle/mlp.py), training on move traces of
+the plain method, and what the trained network gains over the plain sweep
+(and over the "no neighbour moved" rule) at a modularity loss within 0.5%."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_2411_02268_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2411_02268_gb300 import _build
+    _build.build()
+    from paper_2411_02268_gb300 import cd
+    return cd, torch
+
+
+def model_arrays(cd, m):
+    W1, b1, w2, b2 = m.to_numpy()
+    return mlp.to_half(W1), b1, mlp.to_half(w2), b2
+
+
+def test_features_match_oracle(env):
+    cd, torch = env
+    g = gen.rmat(12, 16, wmax=16, seed=3)
+    rng = np.random.default_rng(0)
+    lab = rng.integers(0, 300, g.n).astype(np.uint32)
+    moved = (rng.random(g.n) < 0.3).astype(np.uint8)
+    since = rng.integers(0, 20, g.n).astype(np.uint8)
+    attach = rng.random(g.n).astype(np.float32)
+    G = cd.Graph.to_device(g)
+    x = cd.cd_features(G, torch.from_numpy(lab.view(np.int32)).cuda(), torch.from_numpy(moved).cuda(),
+                       torch.from_numpy(since).cuda(), torch.from_numpy(attach).cuda())
+    K = oracle.degrees(g)
+    Sig, size = oracle.community_totals(g.n, lab, K)
+    ref = mlp.features(g.degrees(), K, size[lab], Sig[lab], int(K.sum()), moved, since, attach)
+    got = x.cpu().numpy().astype(np.float64)
+    # the kernel rounds float32 results to float16: within one float16 ulp
+    assert np.all(np.abs(got - mlp.to_half(ref)) <= np.abs(ref) * 2.0**-10 + 1e-7)
+
+
+def test_forward_and_gradient_match_oracle(env):
+    cd, torch = env
+    rng = np.random.default_rng(1)
+    m = cd.MLP.init(seed=3)
+    x = rng.random((5000, 8)).astype(np.float16)
+    y = (rng.random(5000) < 0.4).astype(np.uint8)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    W1, b1, w2, b2 = model_arrays(cd, m)
+    p = cd.cd_mlp_forward(xd, m).cpu().numpy()
+    pr, _, _ = mlp.forward(x.astype(np.float64), W1, b1, w2, b2)
+    assert np.max(np.abs(p - pr)) < 2e-6
+    loss, grad = cd.cd_mlp_gradient(xd, yd, m)
+    rl = mlp.loss(x.astype(np.float64), y, W1, b1, w2, b2)
+    assert abs(loss - rl) < 1e-5 * max(1.0, abs(rl))
+    dW1, db1, dw2, db2 = mlp.gradients(x.astype(np.float64), y, W1, b1, w2, b2)
+    gW1, gb1, gw2, gb2 = grad.to_numpy()
+    for a, b in ((gW1, dW1), (gb1, db1), (gw2, dw2)):
+        assert np.max(np.abs(a - b)) < 1e-5 + 1e-3 * np.max(np.abs(b))
+    assert abs(gb2 - db2) < 1e-5 + 1e-3 * abs(db2)
+    # deterministic summation order
+    loss2, grad2 = cd.cd_mlp_gradient(xd, yd, m)
+    assert loss2 == loss and np.array_equal(np.ctypeslib.as_array(grad2.W1), np.ctypeslib.as_array(grad.W1))
+
+
+def trained_model(cd, torch):
+    """Train on move traces of the plain method (10k SBM, a small R-MAT and a
+    small rewired grid)."""
+    xs, ys = [], []
+    for g in (gen.sbm_10k(1), gen.rmat(15, 16, wmax=16, seed=5), gen.grid(128, 128, 0.02, 16, seed=7)):
+        x, y = cd.cd_trace(cd.Graph.to_device(g), cd.make_params(k=8), sample_rate=0.5)
+        xs.append(x)
+        ys.append(y)
+    x = torch.cat(xs)
+    y = torch.cat(ys)
+    m = cd.MLP.init(seed=0)
+    loss0, _ = cd.cd_mlp_gradient(x, y, m)
+    loss = cd.cd_mlp_train(x, y, m, steps=300, lr=0.02)
+    return m, x, y, loss0, loss
+
+
+def test_training_lowers_loss(env):
+    cd, torch = env
+    m, x, y, loss0, loss = trained_model(cd, torch)
+    assert len(y) > 10000
+    assert loss < loss0
+    base = float(y.float().mean())
+    # better than predicting the base rate
+    ent = -(base * np.log(base) + (1 - base) * np.log(1 - base))
+    assert loss < ent
+
+
+@pytest.mark.parametrize("gname", ["grid256", "sbm20k"])
+def test_learned_skip_gains_over_plain(env, gname):
+    """On graphs whose vertices settle at different times (a rewired grid, a
+    planted partition) the learned proposal lets the sweeps scan far fewer
+    entries than the plain method, and fewer than the "no neighbour moved"
+    rule, at a modularity loss within 0.5%.  (On R-MAT graphs, where hubs
+    touch most vertices, it saves little: see the design doc.)"""
+    cd, torch = env
+    m, *_ = trained_model(cd, torch)
+    g = gen.grid(256, 256, 0.02, 16, seed=2) if gname == "grid256" else gen.sbm(20000, 200, 0.02, 0.0002, 4, 3)
+    G = cd.Graph.to_device(g)
+    _, q_plain = cd.cd_louvain(G, cd.make_params(k=8))
+    s_plain = cd.cd_last_stats().entries_scanned
+    _, q_learn = cd.cd_louvain(G, cd.make_params(k=8, skip_rule=1, skip_threshold=0.02, skip_model=m))
+    st = cd.cd_last_stats()
+    s_learn = st.entries_scanned
+    assert st.full_sweeps >= 2            # the plain sweep is the fallback and the judge
+    _, q_triv = cd.cd_louvain(G, cd.make_params(k=8, skip_rule=2))
+    s_triv = cd.cd_last_stats().entries_scanned
+    print(f"{gname}: plain Q={q_plain:.5f} scanned={s_plain}; learned Q={q_learn:.5f} scanned={s_learn}; "
+          f"neighbour rule Q={q_triv:.5f} scanned={s_triv}")
+    assert q_learn >= q_plain - 0.005 * abs(q_plain)
+    assert s_learn < 0.5 * s_plain
+    assert s_learn < s_triv
+
+
+def test_skip_rules_keep_labels_valid(env):
+    """Skipping changes which vertices decide, never the validity of the
+    result: dense ids, modularity equal to the oracle's for the labels."""
+    cd, torch = env
+    g = gen.rmat(14, 16, wmax=16, seed=4)
+    for rule in (1, 2):
+        m = cd.MLP.init(seed=1)
+        lab, q = cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=8, skip_rule=rule, skip_model=m))
+        l = lab.cpu().numpy().view(np.uint32)
+        u = np.unique(l)
+        assert u[0] == 0 and u[-1] == len(u) - 1
+        assert q == pytest.approx(float(oracle.modularity_fraction(g, l)), abs=1e-15)

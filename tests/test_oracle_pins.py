@@ -521,3 +521,62 @@ def test_mg_aggregation_pins(seed):
             assert all(got.get((b, a)) == v for (a, b), v in got.items())
         else:
             assert all(mg.offsets[r + 1] - mg.offsets[r] <= 4 for r in range(mg.n))
+
+
+# ---- learned skip proposal: the network's oracle ----------------------------------
+
+def _rand_model(seed):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    return (mlp.to_half(rng.normal(0, 0.5, (32, 8))), rng.normal(0, 0.1, 32),
+            mlp.to_half(rng.normal(0, 0.3, 32)), float(rng.normal()))
+
+
+def test_mlp_forward_hand_value():
+    """One hidden unit active: z = w2 * relu(W1 x + b1) + b2 by hand."""
+    from oracle import mlp
+    W1 = np.zeros((32, 8)); W1[0, 0] = 2.0; W1[1, 1] = -1.0
+    b1 = np.zeros(32); b1[0] = 0.5
+    w2 = np.zeros(32); w2[0] = 3.0; w2[1] = 5.0
+    x = np.array([[1.0, 2.0, 0, 0, 0, 0, 0, 1.0]])
+    p, z, h = mlp.forward(x, W1, b1, w2, -1.0)
+    assert h[0, 0] == 2.5 and h[0, 1] == 0.0
+    assert z[0] == 3.0 * 2.5 - 1.0
+    assert abs(p[0] - 1 / (1 + np.exp(-6.5))) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mlp_gradient_finite_differences(seed):
+    """The analytic gradient of the mean binary cross-entropy matches central
+    differences of the loss in float64."""
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    W1, b1, w2, b2 = _rand_model(seed)
+    x = rng.random((50, 8))
+    y = (rng.random(50) < 0.3).astype(np.float64)
+    dW1, db1, dw2, db2 = mlp.gradients(x, y, W1, b1, w2, b2)
+    eps = 1e-6
+    for (j, q) in [(0, 0), (3, 5), (31, 7), (10, 2)]:
+        Wp, Wm = W1.copy(), W1.copy()
+        Wp[j, q] += eps; Wm[j, q] -= eps
+        num = (mlp.loss(x, y, Wp, b1, w2, b2) - mlp.loss(x, y, Wm, b1, w2, b2)) / (2 * eps)
+        assert abs(num - dW1[j, q]) < 1e-7 + 1e-5 * abs(num)
+    for j in (0, 17, 31):
+        bp, bm = b1.copy(), b1.copy(); bp[j] += eps; bm[j] -= eps
+        num = (mlp.loss(x, y, W1, bp, w2, b2) - mlp.loss(x, y, W1, bm, w2, b2)) / (2 * eps)
+        assert abs(num - db1[j]) < 1e-7 + 1e-5 * abs(num)
+        wp, wm = w2.copy(), w2.copy(); wp[j] += eps; wm[j] -= eps
+        num = (mlp.loss(x, y, W1, b1, wp, b2) - mlp.loss(x, y, W1, b1, wm, b2)) / (2 * eps)
+        assert abs(num - dw2[j]) < 1e-7 + 1e-5 * abs(num)
+    num = (mlp.loss(x, y, W1, b1, w2, b2 + eps) - mlp.loss(x, y, W1, b1, w2, b2 - eps)) / (2 * eps)
+    assert abs(num - db2) < 1e-7 + 1e-5 * abs(num)
+
+
+def test_mlp_features_definition():
+    from oracle import mlp
+    x = mlp.features(deg=[0, 3, 255], K=[0, 6, 1000], size_d=[1, 4, 1], sigma_d=[0, 12, 1000], two_m=4000,
+                     moved_last=[1, 0, 1], since_move=[0, 3, 20], attach=[0.0, 0.25, 1.0])
+    assert x[1, 0] == 2.0 / 16 and x[2, 0] == 8.0 / 16
+    assert x[:, 1].tolist() == [1, 0, 1] and x[:, 2].tolist() == [0, 3 / 8, 1]
+    assert x[1, 3] == np.log2(5) / 24 and x[1, 4] == np.sqrt(12 / 4000) and x[1, 5] == 0.5
+    assert x[:, 6].tolist() == [0.0, 0.25, 1.0] and np.all(x[:, 7] == 1.0) and x[0, 5] == 0.0
