@@ -175,6 +175,92 @@ def oracle_sample(g, k: int, seconds: float, threads: int):
         frac = min(1.0, frac * max(2.0, min(8.0, seconds / max(dt, 1e-3))))
 
 
+def learned_vs_plain(cd, torch, side: int):
+    """Learned skip proposal against the plain method: train on move traces
+    of small graphs, then run Louvain on a side x side grid with 2% of edges
+    rewired, w in [1, 16]."""
+    from paper_2411_02268_gb300 import gen
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    for tg in (gen.sbm_10k(1), gen.rmat(15, 16, wmax=16, seed=5), gen.grid(128, 128, 0.02, 16, seed=7)):
+        x, y = cd.cd_trace(cd.Graph.to_device(tg), cd.make_params(k=8), sample_rate=0.5)
+        xs.append(x)
+        ys.append(y)
+    model = cd.MLP.init(seed=0)
+    loss = cd.cd_mlp_train(torch.cat(xs), torch.cat(ys), model, steps=400, lr=0.02)
+    t_train = time.perf_counter() - t0
+    g = gen.grid(side, side, 0.02, 16, seed=1)
+    G = cd.Graph.to_device(g)
+    out = {"graph": f"grid {side}x{side}, 2% rewired, w in [1,16]", "n": g.n, "nnz": g.nnz,
+           "train_samples": int(sum(len(y) for y in ys)), "train_loss": loss, "train_seconds": round(t_train, 2)}
+    for name, kw in (("plain", {}), ("learned", dict(skip_rule=1, skip_threshold=0.02, skip_model=model)),
+                     ("neighbour_rule", dict(skip_rule=2))):
+        cd.cd_louvain(G, cd.make_params(k=8, **kw))  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, q = cd.cd_louvain(G, cd.make_params(k=8, **kw))
+        torch.cuda.synchronize()
+        st = cd.cd_last_stats()
+        out[name] = {"q": q, "ms": (time.perf_counter() - t) * 1e3, "entries_scanned": int(st.entries_scanned),
+                     "sweeps": int(st.sweeps), "full_sweeps": int(st.full_sweeps)}
+    qp = out["plain"]["q"]
+    for name in ("learned", "neighbour_rule"):
+        out[name]["q_loss_pct"] = (qp - out[name]["q"]) / abs(qp) * 100 if qp else 0.0
+        out[name]["scanned_vs_plain"] = out[name]["entries_scanned"] / max(out["plain"]["entries_scanned"], 1)
+        out[name]["speedup_vs_plain"] = out["plain"]["ms"] / out[name]["ms"]
+    return out
+
+
+def batched_vs_plain(cd, torch, count: int):
+    """Batched Louvain against the plain method run graph by graph, on a batch
+    of `count` planted-partition graphs of uneven size (n log-uniform in
+    [1k, 200k], 10..2000 communities, average degree 8..64, p_in = 10 p_out,
+    w in [1, 16]).  Throughput = CSR entries of all graphs / wall time of the
+    whole detection (all passes), device-resident inputs."""
+    from paper_2411_02268_gb300 import gen
+    t0 = time.perf_counter()
+    gs = gen.sbm_batch(count, seed=1)
+    t_gen = time.perf_counter() - t0
+    dev = [cd.Graph.to_device(g) for g in gs]
+    M = sum(g.nnz for g in gs)
+    N = sum(g.n for g in gs)
+    p = cd.make_params(k=8)
+    cd.cd_louvain_batched(dev[:16], p)  # warm-up
+    for G in dev[:16]:
+        cd.cd_louvain(G, p)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    labs, qb, swb = cd.cd_louvain_batched(dev, p)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    st = cd.cd_last_stats()
+    union = {"sweeps": int(st.sweeps), "passes": int(st.passes), "scratch_bytes": int(st.scratch_bytes)}
+    qp, swp, same = [], [], 0
+    t = time.perf_counter()
+    outs = []
+    for G in dev:
+        lab, q = cd.cd_louvain(G, p)
+        qp.append(q)
+        swp.append(cd.cd_last_stats().sweeps)
+        outs.append(lab)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t
+    for a, b in zip(labs, outs):
+        same += bool(torch.equal(a, b))
+    qb, qp = np.asarray(qb), np.asarray(qp)
+    return {
+        "graphs": count, "n_total": N, "nnz_total": M, "gen_seconds": round(t_gen, 1),
+        "batched": {"ms": tb * 1e3, "gteps": M / tb / 1e9, "q_mean": float(qb.mean()), "union": union},
+        "plain_per_graph": {"ms": tp * 1e3, "gteps": M / tp / 1e9, "q_mean": float(qp.mean()),
+                            "sweeps_total": int(sum(swp))},
+        "speedup_vs_plain": tp / tb,
+        "q_loss_pct": float((qp.mean() - qb.mean()) / abs(qp.mean()) * 100) if qp.mean() else 0.0,
+        "max_abs_dq": float(np.max(np.abs(qb - qp))),
+        "graphs_identical": int(same),
+        "sweeps_identical": bool(np.array_equal(np.asarray(swb), np.asarray(swp))),
+    }
+
+
 def run_reference(args, g, world):
     """CPU oracle arm: each step is a bounded sample of the workload."""
     threads = os.cpu_count() or 1
@@ -209,6 +295,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-side", type=int, default=2048,
+                    help="side of the rewired grid for the learned-skip comparison (0 = skip it)")
+    ap.add_argument("--warm-seconds", type=float, default=1.0,
+                    help="after the warm-up steps, keep stepping (untimed) for this long")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="graphs in the batched-vs-plain comparison (0 = skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -246,6 +338,11 @@ def main():
         return cd.cd_sweep(G, params, cd.MODE_LOUVAIN, lab, labels_out=out)
 
     for _ in range(args.warmup):
+        step()
+    # keep warming until the GPU has run the step for warm_seconds (clocks and
+    # memory power state settle), then time
+    t_w = time.perf_counter()
+    while time.perf_counter() - t_w < args.warm_seconds:
         step()
     torch.cuda.synchronize()
     kern_ms, kern_launches = 0.0, 0
@@ -305,6 +402,13 @@ def main():
                 "traffic": traffic, "kernel": "k_sweep_mg", "kernel_ms": kern_avg_ms,
                 "algorithmic_bytes": ab["bytes"], "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
 
+    learned = None
+    if args.learned_side > 0:
+        learned = learned_vs_plain(cd, torch, args.learned_side)
+    batched = None
+    if args.batch_count > 0:
+        batched = batched_vs_plain(cd, torch, args.batch_count)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -321,7 +425,8 @@ def main():
                        "mode": "louvain", "labels": "singletons", "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas{world}", "scratch_bytes": scratch, "moved": moved,
                        "gen_seconds": round(t_gen, 2)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "learned_vs_plain": learned,
+            "batched_vs_plain": batched,
             "gpu_launches": 7 * args.steps, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

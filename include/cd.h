@@ -138,6 +138,11 @@ typedef struct cd_params {
                              convergence. */
     float skip_threshold;
     const cd_mlp* skip_model; /* host memory, read during the call */
+    int32_t capture;      /* drivers: nonzero = record the launches of one sweep (its
+                             sub-sweeps, commits and, batched, the per-graph stopping rule)
+                             once per level as a CUDA graph and replay it every sweep;
+                             ignored with timing, skip rules or exact rows too long for
+                             shared memory.  Results are the same either way. */
 } cd_params;
 
 typedef struct cd_stats {
@@ -214,6 +219,53 @@ int cd_modularity(const cd_csr* g, const uint32_t* labels, void* stream, double*
  * dense community ids (ascending order of first appearance by id);
  * q_out (host, may be NULL): modularity of the result on the input graph. */
 int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out);
+
+/* Batched Louvain: `ngraphs` independent graphs detected together (the paper
+ * runs one graph at a time; batching is an addition to its method that
+ * changes none of its arithmetic).  The graphs are packed into one disjoint
+ * union whose every graph starts its CSR entries on a multiple of 1024, so
+ * that the sketch kernels give each graph the stream partition of a run on
+ * its own; each sweep of the union is one launch per colour class over all
+ * graphs, with 2m, the stopping rule (moved nobody, summed delta-Q <=
+ * tolerance, max_sweeps) and the pass rule (|V'| = |V| or > aggregation_
+ * tolerance |V|) applied per graph.  Every graph's labels, modularity and
+ * sweep count equal those of cd_louvain on that graph alone with the same
+ * parameters.
+ * graphs: ngraphs CSRs, all in the same memory space (each n < 2^31 - 1,
+ * the sum of n + 1 below 2^31 - 1).  labels_out[g]: graphs[g].n dense
+ * community ids, same memory space as the graphs (may be NULL when n = 0).
+ * q_out, sweeps_out (host, may be NULL): ngraphs modularities and sweep
+ * counts (all passes).  skip_rule and one_scan must be 0.  cd_stats counts
+ * the sweeps and passes of the union. */
+int cd_louvain_batched(const cd_csr* graphs, int ngraphs, const cd_params* p, uint32_t* const* labels_out,
+                       double* q_out, int64_t* sweeps_out);
+
+#define CD_TUNE_MAX_K 8
+
+typedef struct cd_tune_report {
+    double default_ms;                  /* one full sweep of the packed batch, default schedule, k = ks[0] */
+    double sweep_ms[CD_TUNE_MAX_K];     /* candidate i: one full sweep with its tuned schedule */
+    double run_ms[CD_TUNE_MAX_K];       /* candidate i: the whole batched Louvain with that schedule */
+    double q_mean[CD_TUNE_MAX_K];       /* candidate i: mean modularity over the graphs */
+    int32_t trials;                     /* timed sweeps */
+    int32_t chosen;                     /* index of the chosen candidate */
+} cd_tune_report;
+
+/* Autotuner of the batched form (an addition to the paper's method; it
+ * changes no arithmetic, only the schedule and k): packs the graphs as
+ * cd_louvain_batched does, then for every candidate sketch size ks[i] (nks
+ * <= CD_TUNE_MAX_K, each a valid k) tunes the streams per degree band of
+ * the schedule (deg_max bands of p->sched or the default) by coordinate
+ * descent on timed sweeps of the whole batch from singleton labels (each
+ * band, longest rows first, tries half and twice its streams and keeps a
+ * change that is at least 2% faster; median of 3 CUDA-event timings), and
+ * runs batched Louvain with the tuned schedule.  The choice is the fastest
+ * candidate whose mean modularity is within q_tol (relative) of the best
+ * candidate's.  sched_out, k_out (host) receive it; report (host, may be
+ * NULL) the timings.  Timings vary from run to run, so the choice may too;
+ * the results of a given (schedule, k) do not. */
+int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int* ks, int nks, double q_tol,
+                cd_schedule* sched_out, int* k_out, cd_tune_report* report);
 
 /* LPA (Section 3.5, 4.3): synchronous iterations from singleton labels until
  * at most tolerance * n labels change or max_sweeps.  Same outputs. */

@@ -25,7 +25,8 @@ MAX_BUCKETS = 16
 # Symbols declared in include/cd.h.
 SYMBOLS = ("cd_strerror", "cd_last_stats", "cd_default_schedule", "cd_sweep", "cd_modularity",
            "cd_louvain", "cd_lpa", "cd_leiden", "cd_aggregate", "cd_aggregate_mg", "cd_modularity_noalloc",
-           "cd_features", "cd_mlp_forward", "cd_mlp_gradient", "cd_mlp_train", "cd_trace")
+           "cd_features", "cd_mlp_forward", "cd_mlp_gradient", "cd_mlp_train", "cd_trace",
+           "cd_louvain_batched", "cd_autotune")
 
 
 class CSR(ctypes.Structure):
@@ -76,7 +77,7 @@ class Params(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("colors", ctypes.c_int32),
                 ("sub_color", ctypes.c_int32), ("one_scan", ctypes.c_int32), ("agg_k", ctypes.c_int32),
                 ("skip_rule", ctypes.c_int32), ("skip_threshold", ctypes.c_float),
-                ("skip_model", ctypes.POINTER(MLP))]
+                ("skip_model", ctypes.POINTER(MLP)), ("capture", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -86,6 +87,15 @@ class Stats(ctypes.Structure):
                 ("sweep_kernel_ms", ctypes.c_double), ("sweep_kernel_launches", ctypes.c_int64),
                 ("modularity", ctypes.c_double), ("entries_scanned", ctypes.c_int64),
                 ("full_sweeps", ctypes.c_int64), ("cuda_error", ctypes.c_char * 128)]
+
+
+TUNE_MAX_K = 8
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("default_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double * TUNE_MAX_K),
+                ("run_ms", ctypes.c_double * TUNE_MAX_K), ("q_mean", ctypes.c_double * TUNE_MAX_K),
+                ("trials", ctypes.c_int32), ("chosen", ctypes.c_int32)]
 
 
 class ModularityParts(ctypes.Structure):
@@ -140,6 +150,10 @@ def lib():
             L.cd_aggregate_mg.argtypes = [ctypes.POINTER(CSR), P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(Schedule), P, P, P, P, P,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+            L.cd_louvain_batched.argtypes = [ctypes.POINTER(CSR), ctypes.c_int, ctypes.POINTER(Params), P, P, P]
+            L.cd_autotune.argtypes = [ctypes.POINTER(CSR), ctypes.c_int, ctypes.POINTER(Params), P, ctypes.c_int,
+                                      ctypes.c_double, ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(TuneReport)]
             for name in SYMBOLS:
                 if name != "cd_strerror":
                     getattr(L, name).restype = ctypes.c_int
@@ -206,7 +220,7 @@ def current_stream():
 def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregation_tolerance=0.8,
                 max_sweeps=20, max_passes=10, schedule: Schedule | None = None, stream=None,
                 timing=False, colors=0, sub_color=0, one_scan=False, agg_k=0, skip_rule=0,
-                skip_threshold=0.5, skip_model: "MLP | None" = None) -> Params:
+                skip_threshold=0.5, skip_model: "MLP | None" = None, capture=True) -> Params:
     p = Params()
     p.k, p.subtract = int(k), int(subtract)
     p.tolerance, p.tolerance_drop, p.aggregation_tolerance = tolerance, tolerance_drop, aggregation_tolerance
@@ -221,6 +235,7 @@ def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregatio
     p.skip_rule = int(skip_rule)
     p.skip_threshold = float(skip_threshold)
     p.skip_model = ctypes.pointer(skip_model) if skip_model is not None else None
+    p.capture = int(bool(capture))
     p._keep_model = skip_model
     p._keep = schedule
     return p
@@ -308,6 +323,42 @@ def _whole(fn_name, g: Graph, params: Params, labels_out=None):
 
 def cd_louvain(g: Graph, params: Params, labels_out=None):
     return _whole("cd_louvain", g, params, labels_out)
+
+
+def cd_louvain_batched(graphs, params: Params, labels_out=None):
+    """Louvain on a list of graphs (all device or all host) in one batched
+    call.  Returns (labels per graph, modularity per graph as a numpy array,
+    sweeps per graph as a numpy array)."""
+    G = len(graphs)
+    if labels_out is None:
+        labels_out = []
+        for g in graphs:
+            if g.memory == MEM_DEVICE:
+                import torch
+                labels_out.append(torch.empty(max(g.n, 1), dtype=torch.int32, device=g.offsets.device))
+            else:
+                labels_out.append(np.empty(max(g.n, 1), dtype=np.uint32))
+    csrs = (CSR * G)(*[g.csr() for g in graphs])
+    outs = (ctypes.c_void_p * G)(*[_ptr(x) for x in labels_out])
+    q = np.zeros(G, dtype=np.float64)
+    sw = np.zeros(G, dtype=np.int64)
+    _check(lib().cd_louvain_batched(csrs, G, ctypes.byref(params), ctypes.addressof(outs), q.ctypes.data,
+                                    sw.ctypes.data), "cd_louvain_batched")
+    return [x[:g.n] for x, g in zip(labels_out, graphs)], q, sw
+
+
+def cd_autotune(graphs, params: Params, ks=(4, 8, 16), q_tol=0.005):
+    """Tunes the schedule and picks k for a batch (see cd.h).  Returns
+    (Schedule, k, TuneReport)."""
+    G = len(graphs)
+    csrs = (CSR * G)(*[g.csr() for g in graphs])
+    karr = (ctypes.c_int * len(ks))(*[int(k) for k in ks])
+    sched = Schedule()
+    k_out = ctypes.c_int()
+    rep = TuneReport()
+    _check(lib().cd_autotune(csrs, G, ctypes.byref(params), ctypes.addressof(karr), len(ks), float(q_tol),
+                             ctypes.byref(sched), ctypes.byref(k_out), ctypes.byref(rep)), "cd_autotune")
+    return sched, k_out.value, rep
 
 
 def cd_lpa(g: Graph, params: Params, labels_out=None):

@@ -2,11 +2,13 @@
 // scratch, the launch sequence of one sweep, modularity, and host-memory
 // staging.  Every entry point returns a status code and never aborts.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
+#include "batch.cuh"
 #include "cd_internal.cuh"
 
 using namespace cdk;
@@ -160,6 +162,10 @@ struct Level {
     uint32_t* size = nullptr;
     uint32_t* verts = nullptr;
     uint32_t* movers = nullptr;
+    const uint32_t* cid = nullptr;  // colour id of every vertex (null: the vertex id)
+    bool reuse = false;   // prepare_level keeps the buffers of an earlier call (schedule trials)
+    uint32_t *tc = nullptr, *to = nullptr;  // bucketing scratch
+    int64_t* dstarts = nullptr;
     BucketTable bt;     // bucket layout; ranges of colour class 0
     int colors = 1;
     std::vector<int64_t> starts;  // (colour, bucket) range starts, colors * nb + 1
@@ -206,21 +212,27 @@ int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cud
 // 2m, max K and the bucket ranges.
 int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, bool exact,
                   const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s) {
-    CD_TRY(sc.get(&L.K, L.n));
-    CD_TRY(sc.get(&L.Sigma, L.n));
-    CD_TRY(sc.get(&L.size, L.n));
-    CD_TRY(sc.get(&L.verts, L.n));
+    const bool fresh = !L.reuse || !L.K;
+    if (fresh) {
+        CD_TRY(sc.get(&L.K, L.n));
+        CD_TRY(sc.get(&L.Sigma, L.n));
+        CD_TRY(sc.get(&L.size, L.n));
+        CD_TRY(sc.get(&L.verts, L.n));
+    }
     L.bt = exact ? exact_table() : table_from(sched);
     L.colors = colors;
     const int nkeys = colors * L.bt.nb;
     int64_t ntiles = bucket_tiles(L.n);
-    uint32_t *tc, *to;
-    int64_t* starts;
-    CD_TRY(sc.get(&tc, ntiles * nkeys));
-    CD_TRY(sc.get(&to, ntiles * nkeys));
-    CD_TRY(sc.get(&starts, nkeys + 1));
+    if (fresh) {
+        const int64_t cap = L.reuse ? (int64_t)kMaxColors * CD_MAX_BUCKETS : nkeys;
+        CD_TRY(sc.get(&L.tc, ntiles * cap));
+        CD_TRY(sc.get(&L.to, ntiles * cap));
+        CD_TRY(sc.get(&L.dstarts, cap + 1));
+    }
+    uint32_t *tc = L.tc, *to = L.to;
+    int64_t* starts = L.dstarts;
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
-    CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, colors, tc, to, starts, L.verts, labels, labels_out_copy,
+    CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, colors, L.cid, tc, to, starts, L.verts, labels, labels_out_copy,
                           dglob, s));
     HostGlobals hg;
     CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
@@ -439,7 +451,7 @@ int aggregate_mg_level(const Level& L, const uint32_t* dense, int64_t nc, int k,
     CD_TRY(sc.get(&tc, ntiles * nkeys));
     CD_TRY(sc.get(&to, ntiles * nkeys));
     CD_TRY(sc.get(&starts, nkeys + 1));
-    CD_CUDA(launch_bucket(coff, nc, m, C.bt, 1, tc, to, starts, C.verts, nullptr, nullptr, dglob, s));
+    CD_CUDA(launch_bucket(coff, nc, m, C.bt, 1, nullptr, tc, to, starts, C.verts, nullptr, nullptr, dglob, s));
     HostGlobals hg;
     CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
     C.starts.assign(hg.starts, hg.starts + nkeys + 1);
@@ -565,6 +577,44 @@ int stage_model(const cd_mlp* m, Scratch& sc, float** dparam, cudaStream_t s) {
     return CD_OK;
 }
 
+// Per-graph state of the batched form during one level (a disjoint union of
+// graphs, see batch.cu).  Device arrays have G + 1 entries (the last one is
+// the sentinel graph of the padding vertices, which never decides).
+struct BatchLevel {
+    int G = 0;
+    const uint32_t* gid = nullptr;   // graph of every vertex of the level
+    const int64_t* vb = nullptr;     // first vertex of every graph (device, G)
+    const int64_t* nv = nullptr;     // vertices of every graph (device, G)
+    unsigned long long* two_m_g = nullptr;
+    uint8_t* gdone = nullptr;
+    uint32_t* gsweeps = nullptr;
+    unsigned long long* gstat = nullptr;  // moved, gain_lo, gain_hi (3 x (G + 1))
+    std::vector<uint8_t> finished;   // host: graphs whose passes have ended
+};
+
+// One sweep replayed from a CUDA graph (see local_move).
+struct Replay {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~Replay() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+// True when launch_sweep on level L enqueues kernels only (no host sync).
+bool sweep_is_async(const Level& L, int k) {
+    if (k > 0) return true;
+    for (int b = 0; b < kExactBuckets; ++b)
+        if (kExact[b].global && L.starts.size() > 0) {
+            for (int c = 0; c < L.colors; ++c)
+                if (L.starts[(size_t)c * L.bt.nb + b + 1] > L.starts[(size_t)c * L.bt.nb + b]) return false;
+        }
+    return true;
+}
+
 // Local-moving phase on level L from `init` labels (singletons when null):
 // every sweep is `colors` sub-sweeps (sub-sweep c decides the vertices of
 // colour class c from the state left by the previous ones), each followed by
@@ -572,11 +622,14 @@ int stage_model(const cd_mlp* m, Scratch& sc, float** dparam, cudaStream_t s) {
 // delta-Q is at most tol (Louvain), at most tol * n labels change (LPA), or
 // max_sweeps.  With a skip rule, sweeps after the first decide only the
 // proposed vertices; a proposal sweep that moves nobody or gains at most tol
-// is followed by a full sweep, which decides convergence.  Returns the final
-// labels in *labels (a scratch buffer).
+// is followed by a full sweep, which decides convergence.  In the batched
+// form (B) the stopping rule is applied per graph on the device and the
+// phase ends when every graph has stopped.  With p->capture the launches of
+// one sweep are recorded once as a CUDA graph and replayed every sweep.
+// Returns the final labels in *labels (a scratch buffer).
 int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_schedule& sched, Scratch& sc,
                Globals* dglob, cudaStream_t s, const uint32_t* init, uint32_t** labels, int64_t* sweeps_out,
-               Trace* trace = nullptr) {
+               Trace* trace = nullptr, BatchLevel* B = nullptr) {
     uint32_t *la, *lb;
     CD_TRY(sc.get(&la, L.n));
     CD_TRY(sc.get(&lb, L.n));
@@ -615,10 +668,69 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         CD_TRY(sc.get(&ttiles, scan_tiles(L.n) + 1));
     }
     if (rule == 1) CD_TRY(stage_model(p->skip_model, sc, &param, s));
+    const int G = B ? B->G : 0;
+    if (B) {
+        CD_CUDA(launch_graph_two_m(L.K, B->vb, B->nv, G, B->two_m_g, s));
+        std::vector<uint8_t> d0(B->finished);
+        d0.push_back(1);  // sentinel graph
+        if (p->max_sweeps == 0) std::fill(d0.begin(), d0.end(), (uint8_t)1);
+        CD_CUDA(cudaMemcpyAsync(B->gdone, d0.data(), (size_t)G + 1, cudaMemcpyHostToDevice, s));
+        CD_CUDA(cudaMemsetAsync(B->gsweeps, 0, sizeof(uint32_t) * ((size_t)G + 1), s));
+        CD_CUDA(cudaStreamSynchronize(s));  // d0 must outlive the copy
+    }
     std::vector<Timer> tms((size_t)colors);
     for (auto& t : tms) CD_TRY(t.init(p->timing != 0));
     const size_t stat_off = offsetof(Globals, moved);
     const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
+    // the launches of one sweep on stream st
+    auto enqueue = [&](cudaStream_t st, bool use_mask) -> int {
+        CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, st));
+        if (B) {
+            CD_CUDA(cudaMemsetAsync(B->gstat, 0, sizeof(unsigned long long) * 3 * ((size_t)G + 1), st));
+            CD_CUDA(cudaMemsetAsync(&dglob->count, 0, sizeof(unsigned long long), st));
+        }
+        for (int c = 0; c < colors; ++c) {
+            // sub-sweep c: vertices of colour c decide from la and write lb; the
+            // movers' new labels are then copied into la for sub-sweep c+1
+            CD_CUDA(cudaMemcpyAsync(&dglob->mark, &dglob->moved, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToDevice, st));
+            Level Lc = L;
+            Lc.bt = L.table_for(c);
+            SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract);
+            a.one_scan = p->one_scan;
+            a.attach = attach;
+            if (B) {
+                a.gid = B->gid;
+                a.two_m_g = B->two_m_g;
+                a.gdone = B->gdone;
+                a.g_moved = B->gstat;
+                a.g_gain_lo = B->gstat + (G + 1);
+                a.g_gain_hi = B->gstat + 2 * (G + 1);
+            }
+            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].a, st));
+            CD_TRY(launch_sweep(Lc, a, p->k, sc, st));
+            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, st));
+            CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, st));
+            CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, st));
+        }
+        if (B)
+            CD_CUDA(launch_batch_converge(G, B->two_m_g, B->gstat, B->gstat + (G + 1), B->gstat + 2 * (G + 1), tol,
+                                          p->max_sweeps, B->gsweeps, B->gdone, dglob, st));
+        return CD_OK;
+    };
+    Replay rp;
+    if (p->capture && !track && !p->timing && sweep_is_async(L, p->k)) {
+        // record one sweep on a private stream; replays go to s
+        CD_CUDA(cudaStreamCreateWithFlags(&rp.cs, cudaStreamNonBlocking));
+        CD_CUDA(cudaStreamBeginCapture(rp.cs, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue(rp.cs, false);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(rp.cs, &gr);
+        rp.graph = gr;
+        CD_TRY(rc);
+        CD_CUDA(ec);
+        CD_CUDA(cudaGraphInstantiate(&rp.exec, rp.graph, 0));
+    }
     int64_t sw = 0;
     bool force_full = false;
     for (; sw < p->max_sweeps;) {
@@ -629,28 +741,13 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
             CD_CUDA(launch_mark_neighbours(L.off, L.cols, L.movers, dglob, active, s));
         }
         if ((use_mask && rule == 1) || (trace && sw > 0)) {
-            CD_CUDA(launch_features(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, L.n,
-                                    x, s));
+            CD_CUDA(launch_features(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, true,
+                                    L.n, x, s));
             if (use_mask) CD_CUDA(launch_mlp_forward(x, L.n, param, nullptr, active, p->skip_threshold, s));
         }
         if (track) CD_CUDA(cudaMemcpyAsync(before, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
-        CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
-        for (int c = 0; c < colors; ++c) {
-            // sub-sweep c: vertices of colour c decide from la and write lb; the
-            // movers' new labels are then copied into la for sub-sweep c+1
-            CD_CUDA(cudaMemcpyAsync(&dglob->mark, &dglob->moved, sizeof(unsigned long long),
-                                    cudaMemcpyDeviceToDevice, s));
-            Level Lc = L;
-            Lc.bt = L.table_for(c);
-            SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract);
-            a.one_scan = p->one_scan;
-            a.attach = attach;
-            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].a, s));
-            CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
-            if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, s));
-            CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
-            CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
-        }
+        if (rp.exec) CD_CUDA(cudaGraphLaunch(rp.exec, s));
+        else CD_TRY(enqueue(s, use_mask));
         if (track) CD_CUDA(launch_move_state(before, la, L.n, moved_last, since_move, s));
         HostGlobals hg;
         if (trace && sw > 0) {
@@ -676,6 +773,10 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         g_stats.gain_hi = hg.g.gain_hi;
         g_stats.entries_scanned += (int64_t)hg.g.scanned;
         if (!use_mask) g_stats.full_sweeps += 1;
+        if (B) {
+            if (hg.g.count == 0) break;  // every graph has stopped
+            continue;
+        }
         bool done = hg.g.moved == 0;
         if (!done) {
             if (mode == CD_MODE_LPA) {
@@ -786,6 +887,61 @@ int emit_labels(const cd_csr* g, const uint32_t* dense, uint32_t* labels_out, cu
     cudaMemcpyKind kind = g->memory == CD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     CD_CUDA(cudaMemcpyAsync(labels_out, dense, sizeof(uint32_t) * g->n, kind, s));
     CD_CUDA(cudaStreamSynchronize(s));
+    return CD_OK;
+}
+
+// Packs `G` input graphs (all in one memory space) into one disjoint union
+// (batch.cu): graph g at vertices [vb0_g, vb0_g + n_g] (the last one its
+// padding vertex), entries from a multiple of kPackAlign.  Fills the level
+// `in` (with colour ids = ids inside each graph), the graph of every vertex
+// (*gid0) and the per-graph layout vectors.
+int pack_union(const cd_csr* graphs, int G, Scratch& sc, Globals* dglob, cudaStream_t s, std::vector<PackGraph>& pg,
+               std::vector<int64_t>& vb0, std::vector<int64_t>& n0, std::vector<int64_t>& tstart, Level* in,
+               uint32_t** gid0, uint32_t** lid0) {
+    pg.assign((size_t)G, PackGraph());
+    vb0.assign((size_t)G, 0);
+    n0.assign((size_t)G, 0);
+    tstart.assign((size_t)G + 1, 0);
+    int64_t V = 0, E = 0;
+    for (int g = 0; g < G; ++g) {
+        const cd_csr& c = graphs[g];
+        PackGraph& q = pg[(size_t)g];
+        std::memset(&q, 0, sizeof(q));
+        if (c.memory == CD_MEM_HOST) {
+            int64_t* off; int32_t* cols; uint32_t* w;
+            CD_TRY(stage_in(c.offsets, c.n + 1, &off, sc));
+            CD_TRY(stage_in(c.cols, c.nnz, &cols, sc));
+            CD_TRY(stage_in(c.weights, c.nnz, &w, sc));
+            q.off = off; q.cols = cols; q.w = w;
+        } else {
+            q.off = c.offsets; q.cols = c.cols; q.w = c.weights;
+        }
+        q.vsrc0 = 0; q.n = c.n; q.nnz = c.nnz;
+        q.vbase = V; q.ebase = E;
+        q.pad = (E + c.nnz + kPackAlign - 1) / kPackAlign * kPackAlign - (E + c.nnz);
+        q.col_shift = V; q.check_first = 1;
+        vb0[(size_t)g] = V;
+        n0[(size_t)g] = c.n;
+        V += c.n + 1;
+        E += c.nnz + q.pad;
+        tstart[(size_t)g + 1] = tstart[(size_t)g] + pack_tiles(q);
+        if (V >= 0x7FFFFFFFLL) return CD_EINVAL;  // union ids must fit int32 columns
+    }
+    int64_t* uoff; int32_t* ucols; uint32_t* uw;
+    PackGraph* dpg; int64_t* dts;
+    CD_TRY(sc.get(&uoff, V + 1));
+    CD_TRY(sc.get(&ucols, E));
+    CD_TRY(sc.get(&uw, E));
+    CD_TRY(sc.get(gid0, V));
+    CD_TRY(sc.get(lid0, V));
+    CD_TRY(stage_in(pg.data(), G, &dpg, sc));
+    CD_TRY(stage_in(tstart.data(), G + 1, &dts, sc));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(launch_pack(dpg, dts, G, tstart[(size_t)G], uoff, ucols, uw, *gid0, *lid0, V, E, dglob, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    *in = Level();
+    in->n = V; in->nnz = E; in->off = uoff; in->cols = ucols; in->w = uw; in->cid = *lid0;
     return CD_OK;
 }
 
@@ -1007,6 +1163,368 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
     return CD_OK;
 }
 
+int cd_louvain_batched(const cd_csr* graphs, int ngraphs, const cd_params* p, uint32_t* const* labels_out,
+                       double* q_out, int64_t* sweeps_out) {
+    reset_stats();
+    if (!graphs || ngraphs < 1 || !labels_out) return CD_EINVAL;
+    CD_TRY(check_driver_params(p));
+    if (p->one_scan || p->skip_rule) return CD_EINVAL;
+    const int G = ngraphs;
+    const int mem = graphs[0].memory;
+    for (int g = 0; g < G; ++g) {
+        CD_TRY(check_csr(&graphs[g]));
+        if (graphs[g].memory != mem) return CD_EINVAL;
+        if (graphs[g].n > 0 && !labels_out[g]) return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule sched;
+    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    Scratch sc(s);
+    Globals* dglob;
+    CD_TRY(sc.get(&dglob, 1));
+    std::vector<PackGraph> pg;
+    std::vector<int64_t> vb0, n0, tstart;
+    Level in;
+    uint32_t *gid0, *lid0;
+    CD_TRY(pack_union(graphs, G, sc, dglob, s, pg, vb0, n0, tstart, &in, &gid0, &lid0));
+    const int64_t V = in.n;
+    // ---- per-graph state
+    BatchLevel bl;
+    bl.G = G;
+    int64_t *dvb, *dnv, *ddummy;
+    uint32_t* ddense_dummy;
+    CD_TRY(sc.get(&bl.two_m_g, G + 1));
+    CD_TRY(sc.get(&bl.gdone, G + 1));
+    CD_TRY(sc.get(&bl.gsweeps, G + 1));
+    CD_TRY(sc.get(&bl.gstat, 3 * (G + 1)));
+    CD_TRY(sc.get(&dvb, G));
+    CD_TRY(sc.get(&dnv, G));
+    CD_TRY(sc.get(&ddummy, G));
+    CD_TRY(sc.get(&ddense_dummy, G));
+    bl.vb = dvb;
+    bl.nv = dnv;
+    std::vector<int64_t> vb(vb0), nv(n0), dummy((size_t)G), gsw((size_t)G, 0);
+    for (int g = 0; g < G; ++g) dummy[(size_t)g] = vb0[(size_t)g] + n0[(size_t)g];
+    std::vector<uint8_t> finished((size_t)G);
+    for (int g = 0; g < G; ++g) finished[(size_t)g] = n0[(size_t)g] == 0;
+    uint32_t* top;
+    CD_TRY(sc.get(&top, V));
+    CD_CUDA(launch_iota(top, V, s));
+    Level cur = in;
+    const uint32_t* gid = gid0;
+    double tol = p->tolerance;
+    auto all_finished = [&]() {
+        for (uint8_t f : finished) if (!f) return false;
+        return true;
+    };
+    for (int pass = 0; pass < p->max_passes && !all_finished(); ++pass) {
+        bl.gid = gid;
+        bl.finished = finished;
+        CD_CUDA(cudaMemcpyAsync(dvb, vb.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s));
+        CD_CUDA(cudaMemcpyAsync(dnv, nv.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s));
+        uint32_t* lab;
+        int64_t sw = 0;
+        CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, nullptr, &lab, &sw, nullptr, &bl));
+        g_stats.sweeps += sw;
+        g_stats.passes += 1;
+        std::vector<uint32_t> gs((size_t)G);
+        CD_CUDA(cudaMemcpyAsync(gs.data(), bl.gsweeps, sizeof(uint32_t) * G, cudaMemcpyDeviceToHost, s));
+        uint32_t* dense;
+        CD_TRY(sc.get(&dense, cur.n));
+        int64_t nc = 0;
+        CD_TRY(renumber_level(cur, lab, dense, sc, dglob, &nc, s));  // synchronises s
+        for (int g = 0; g < G; ++g)
+            if (!finished[(size_t)g]) gsw[(size_t)g] += gs[(size_t)g];
+        CD_CUDA(launch_compose(top, in.n, dense, s));
+        // every graph's communities: a contiguous dense range ending at its
+        // padding vertex
+        std::vector<uint32_t> dd((size_t)G);
+        CD_CUDA(cudaMemcpyAsync(ddummy, dummy.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, s));
+        CD_CUDA(launch_gather_u32(dense, ddummy, G, ddense_dummy, s));
+        CD_CUDA(cudaMemcpyAsync(dd.data(), ddense_dummy, sizeof(uint32_t) * G, cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaStreamSynchronize(s));
+        for (int g = 0; g < G; ++g) {
+            const int64_t cb = g == 0 ? 0 : (int64_t)dd[(size_t)g - 1] + 1;
+            const int64_t ncg = (int64_t)dd[(size_t)g] - cb;
+            const size_t u = (size_t)g;
+            if (!finished[u] && (ncg == nv[u] || (double)ncg > p->aggregation_tolerance * (double)nv[u]))
+                finished[u] = 1;
+            vb[u] = cb;
+            nv[u] = ncg;
+            dummy[u] = (int64_t)dd[u];
+        }
+        if (pass + 1 >= p->max_passes || all_finished()) break;
+        Level next;
+        if (p->agg_k > 0)
+            CD_TRY(aggregate_mg_level(cur, dense, nc, p->agg_k, false, p->subtract, sched, sc, dglob, s, nullptr,
+                                      nullptr, nullptr, &next));
+        else
+            CD_TRY(aggregate_level(cur, dense, nc, sc, dglob, s, nullptr, nullptr, nullptr, &next));
+        // re-pack the super-vertex graph with aligned entry bases
+        std::vector<int64_t> idx((size_t)2 * G), ob((size_t)2 * G);
+        for (int g = 0; g < G; ++g) {
+            idx[(size_t)2 * g] = vb[(size_t)g];
+            idx[(size_t)2 * g + 1] = vb[(size_t)g] + nv[(size_t)g];
+        }
+        int64_t *didx, *dob;
+        CD_TRY(stage_in(idx.data(), 2 * G, &didx, sc));
+        CD_TRY(sc.get(&dob, 2 * G));
+        CD_CUDA(launch_gather_i64(next.off, didx, 2 * G, dob, s));
+        CD_CUDA(cudaMemcpyAsync(ob.data(), dob, sizeof(int64_t) * 2 * G, cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaStreamSynchronize(s));
+        int64_t E2 = 0;
+        tstart[0] = 0;
+        for (int g = 0; g < G; ++g) {
+            PackGraph& q = pg[(size_t)g];
+            std::memset(&q, 0, sizeof(q));
+            q.off = next.off; q.cols = next.cols; q.w = next.w;
+            q.vsrc0 = vb[(size_t)g]; q.n = nv[(size_t)g];
+            q.nnz = ob[(size_t)2 * g + 1] - ob[(size_t)2 * g];
+            q.vbase = vb[(size_t)g]; q.ebase = E2;
+            q.pad = (E2 + q.nnz + kPackAlign - 1) / kPackAlign * kPackAlign - (E2 + q.nnz);
+            q.col_shift = 0; q.check_first = 0;
+            E2 += q.nnz + q.pad;
+            tstart[(size_t)g + 1] = tstart[(size_t)g] + pack_tiles(q);
+        }
+        Level packed;
+        int64_t* uoff; int32_t* ucols; uint32_t* uw;
+        uint32_t *gidn, *lidn;
+        PackGraph* dpg; int64_t* dts;
+        CD_TRY(sc.get(&uoff, nc + 1));
+        CD_TRY(sc.get(&ucols, E2));
+        CD_TRY(sc.get(&uw, E2));
+        CD_TRY(sc.get(&gidn, nc));
+        CD_TRY(sc.get(&lidn, nc));
+        CD_TRY(stage_in(pg.data(), G, &dpg, sc));
+        CD_TRY(stage_in(tstart.data(), G + 1, &dts, sc));
+        CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+        CD_CUDA(launch_pack(dpg, dts, G, tstart[(size_t)G], uoff, ucols, uw, gidn, lidn, nc, E2, dglob, s));
+        HostGlobals hg;
+        CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+        packed.n = nc; packed.nnz = E2; packed.off = uoff; packed.cols = ucols; packed.w = uw; packed.cid = lidn;
+        cur = packed;
+        gid = gidn;
+        tol /= p->tolerance_drop;
+    }
+    // ---- outputs: labels inside every graph, modularity on every input
+    int64_t* dcb;
+    uint32_t *loc, *qlab;
+    CD_TRY(stage_in(vb.data(), G, &dcb, sc));
+    int64_t *dvb0, *dn0;
+    CD_TRY(stage_in(vb0.data(), G, &dvb0, sc));
+    CD_TRY(stage_in(n0.data(), G, &dn0, sc));
+    CD_TRY(sc.get(&loc, V));
+    CD_TRY(sc.get(&qlab, V));
+    CD_CUDA(launch_batch_labels(top, gid0, V, G, dvb0, dcb, loc, qlab, s));
+    uint64_t *K, *Sig;
+    uint32_t* sz;
+    unsigned long long* acc;
+    CD_TRY(sc.get(&K, V));
+    CD_TRY(sc.get(&Sig, V));
+    CD_TRY(sc.get(&sz, V));
+    CD_TRY(sc.get(&acc, 3 * G));
+    CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
+    CD_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 3 * G, s));
+    CD_CUDA(launch_degrees(in.off, in.w, V, in.nnz, K, dglob, s));
+    CD_CUDA(launch_totals(qlab, K, V, Sig, sz, dglob, s));
+    CD_CUDA(launch_graph_two_m(K, dvb0, dn0, G, bl.two_m_g, s));
+    CD_CUDA(launch_batch_modularity(in.off, in.cols, in.w, qlab, Sig, dvb0, dn0, G, acc, s));
+    std::vector<unsigned long long> hacc((size_t)3 * G), htm((size_t)G);
+    CD_CUDA(cudaMemcpyAsync(hacc.data(), acc, sizeof(unsigned long long) * 3 * G, cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(htm.data(), bl.two_m_g, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, s));
+    const cudaMemcpyKind kind = mem == CD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int g = 0; g < G; ++g)
+        if (n0[(size_t)g] > 0)
+            CD_CUDA(cudaMemcpyAsync(labels_out[g], loc + vb0[(size_t)g], sizeof(uint32_t) * n0[(size_t)g], kind, s));
+    HostGlobals hg;
+    CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
+    int64_t ncom = 0;
+    for (int g = 0; g < G; ++g) {
+        ncom += nv[(size_t)g];
+        const u128 sq = ((u128)hacc[(size_t)3 * g + 2] << 64) | (u128)hacc[(size_t)3 * g + 1];
+        const u128 tm = htm[(size_t)g];
+        double q = 0.0;
+        if (tm > 0) {
+            const i128 num = (i128)(tm * (u128)hacc[(size_t)3 * g]) - (i128)sq;
+            q = (double)((long double)num / ((long double)tm * (long double)tm));
+        }
+        if (q_out) q_out[g] = q;
+        if (sweeps_out) sweeps_out[g] = gsw[(size_t)g];
+    }
+    g_stats.communities = ncom;
+    return CD_OK;
+}
+
+int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int* ks, int nks, double q_tol,
+                cd_schedule* sched_out, int* k_out, cd_tune_report* report) {
+    reset_stats();
+    if (!graphs || ngraphs < 1 || !ks || nks < 1 || nks > CD_TUNE_MAX_K || !sched_out || !k_out) return CD_EINVAL;
+    if (!(q_tol >= 0.0)) return CD_EINVAL;
+    CD_TRY(check_driver_params(p));
+    for (int i = 0; i < nks; ++i) {
+        cd_params pk = *p;
+        pk.k = ks[i];
+        CD_TRY(check_params(&pk));
+    }
+    const int G = ngraphs;
+    const int mem = graphs[0].memory;
+    for (int g = 0; g < G; ++g) {
+        CD_TRY(check_csr(&graphs[g]));
+        if (graphs[g].memory != mem) return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)p->stream;
+    cd_schedule base;
+    if (p->sched) base = *p->sched; else default_schedule(&base);
+    cd_tune_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    std::vector<cd_schedule> tuned((size_t)nks, base);
+    int64_t V = 0;
+    {
+        Scratch sc(s);
+        Globals* dglob;
+        CD_TRY(sc.get(&dglob, 1));
+        std::vector<PackGraph> pg;
+        std::vector<int64_t> vb0, n0, tstart;
+        Level L;
+        uint32_t *gid0, *lid0;
+        CD_TRY(pack_union(graphs, G, sc, dglob, s, pg, vb0, n0, tstart, &L, &gid0, &lid0));
+        V = L.n;
+        L.reuse = true;
+        uint32_t *la, *lb;
+        CD_TRY(sc.get(&la, V));
+        CD_TRY(sc.get(&lb, V));
+        CD_TRY(sc.get(&L.movers, V));
+        CD_CUDA(launch_iota(la, V, s));
+        int64_t *dvb, *dnv;
+        CD_TRY(stage_in(vb0.data(), G, &dvb, sc));
+        CD_TRY(stage_in(n0.data(), G, &dnv, sc));
+        unsigned long long *two_m_g, *gstat;
+        uint8_t* gdone;
+        CD_TRY(sc.get(&two_m_g, G + 1));
+        CD_TRY(sc.get(&gstat, 3 * (G + 1)));
+        CD_TRY(sc.get(&gdone, G + 1));
+        CD_CUDA(cudaMemsetAsync(gdone, 0, (size_t)G + 1, s));
+        CD_CUDA(cudaMemsetAsync(gdone + G, 1, 1, s));
+        Timer tm;
+        CD_TRY(tm.init(true));
+        const size_t stat_off = offsetof(Globals, moved);
+        const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
+        // median time of one full sweep of the batch with schedule sc_try and k
+        auto time_sweep = [&](const cd_schedule& st, int k, double* ms_out) -> int {
+            CD_TRY(prepare_level(L, la, lb, k == 0, st, 1, sc, dglob, s));
+            CD_CUDA(launch_graph_two_m(L.K, dvb, dnv, G, two_m_g, s));
+            SweepArgs a = make_args(L, la, lb, nullptr, nullptr, dglob, CD_MODE_LOUVAIN, p->subtract);
+            a.gid = gid0;
+            a.two_m_g = two_m_g;
+            a.gdone = gdone;
+            a.g_moved = gstat;
+            a.g_gain_lo = gstat + (G + 1);
+            a.g_gain_hi = gstat + 2 * (G + 1);
+            float t[3];
+            for (int r = 0; r < 3; ++r) {
+                CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
+                CD_CUDA(cudaEventRecord(tm.a, s));
+                CD_TRY(launch_sweep(L, a, k, sc, s));
+                CD_CUDA(cudaEventRecord(tm.b, s));
+                CD_CUDA(cudaEventSynchronize(tm.b));
+                CD_CUDA(cudaEventElapsedTime(&t[r], tm.a, tm.b));
+                rep.trials += 1;
+            }
+            std::sort(t, t + 3);
+            *ms_out = t[1];
+            HostGlobals hg;
+            return read_globals(dglob, nullptr, 0, &hg, s);
+        };
+        CD_TRY(time_sweep(base, ks[0], &rep.default_ms));
+        for (int i = 0; i < nks; ++i) {
+            const int k = ks[i];
+            cd_schedule cur = base;
+            double best = 0.0;
+            CD_TRY(time_sweep(cur, k, &best));
+            if (k > 0) {
+                // bands with rows, longest first
+                for (int b = cur.nbuckets - 1; b >= 0; --b) {
+                    bool any = false;
+                    for (size_t q = (size_t)b; q + 1 < L.starts.size(); q += (size_t)L.bt.nb)
+                        if (L.starts[q + 1] > L.starts[q]) any = true;
+                    if (!any) continue;
+                    const int l0 = cur.lanes[b];
+                    for (int cand : {l0 / 2, l0 * 2}) {
+                        if (cand < 1 || cand > 256) continue;
+                        cd_schedule t = cur;
+                        t.lanes[b] = cand;
+                        double ms = 0.0;
+                        CD_TRY(time_sweep(t, k, &ms));
+                        if (ms < 0.98 * best) {
+                            best = ms;
+                            cur = t;
+                        }
+                    }
+                }
+            }
+            tuned[(size_t)i] = cur;
+            rep.sweep_ms[i] = best;
+        }
+    }
+    // whole runs with each candidate
+    std::vector<uint32_t*> outs((size_t)G, nullptr);
+    std::vector<std::vector<uint32_t>> hbuf;
+    uint32_t* dbuf = nullptr;
+    if (mem == CD_MEM_HOST) {
+        hbuf.resize((size_t)G);
+        for (int g = 0; g < G; ++g) {
+            hbuf[(size_t)g].resize((size_t)std::max<int64_t>(graphs[g].n, 1));
+            outs[(size_t)g] = hbuf[(size_t)g].data();
+        }
+    } else {
+        CD_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dbuf), sizeof(uint32_t) * (size_t)std::max<int64_t>(V, 1), s));
+        int64_t o = 0;
+        for (int g = 0; g < G; ++g) {
+            outs[(size_t)g] = dbuf + o;
+            o += graphs[g].n + 1;
+        }
+    }
+    std::vector<double> q((size_t)G);
+    int rc = CD_OK;
+    for (int i = 0; i < nks && rc == CD_OK; ++i) {
+        cd_params pk = *p;
+        pk.k = ks[i];
+        pk.sched = &tuned[(size_t)i];
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) { rc = CD_ECUDA; break; }
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); rc = CD_ECUDA; break; }
+        cudaEventRecord(e0, s);
+        rc = cd_louvain_batched(graphs, G, &pk, outs.data(), q.data(), nullptr);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        double qs = 0.0;
+        for (double x : q) qs += x;
+        rep.run_ms[i] = ms;
+        rep.q_mean[i] = qs / G;
+    }
+    const int trials = rep.trials;
+    if (dbuf) cudaFreeAsync(dbuf, s);
+    cudaStreamSynchronize(s);
+    if (rc != CD_OK) return rc;
+    double qbest = rep.q_mean[0];
+    for (int i = 1; i < nks; ++i) qbest = std::max(qbest, rep.q_mean[i]);
+    int pick = -1;
+    for (int i = 0; i < nks; ++i) {
+        if (rep.q_mean[i] < qbest - q_tol * std::fabs(qbest)) continue;
+        if (pick < 0 || rep.run_ms[i] < rep.run_ms[pick]) pick = i;
+    }
+    rep.chosen = pick;
+    rep.trials = trials;
+    *sched_out = tuned[(size_t)pick];
+    *k_out = ks[pick];
+    if (report) *report = rep;
+    return CD_OK;
+}
+
 int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_out) {
     reset_stats();
     CD_TRY(check_csr(g));
@@ -1130,8 +1648,8 @@ int cd_features(const cd_csr* g, const uint32_t* labels, const uint8_t* moved_la
     }
     HostGlobals hg;
     CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
-    CD_CUDA(launch_features(L.off, L.K, labels, L.Sigma, L.size, hg.g.two_m, moved_last, since_move, attach, L.n,
-                            x_out, s));
+    CD_CUDA(launch_features(L.off, L.K, labels, L.Sigma, L.size, hg.g.two_m, moved_last, since_move, attach, false,
+                            L.n, x_out, s));
     CD_CUDA(cudaStreamSynchronize(s));
     return CD_OK;
 }

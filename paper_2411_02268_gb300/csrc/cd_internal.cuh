@@ -53,7 +53,14 @@ struct SweepArgs {
     const uint32_t* bound;    // refine mode only
     uint32_t* labels_out;
     uint32_t* movers;         // optional list of movers (driver), capacity n
-    float* attach;            // optional: K_{i->C_i} / K_i after the decision (skip features)
+    float* attach;            // optional: K_{i->C_i} after the decision, as a float (skip features)
+    // batched form (a disjoint union of graphs); null for a single graph
+    const uint32_t* gid;      // graph of every vertex
+    const unsigned long long* two_m_g;  // 2m of every graph
+    const uint8_t* gdone;     // graphs whose local-moving phase has stopped
+    unsigned long long* g_moved;        // per graph: movers, 128-bit gain sum
+    unsigned long long* g_gain_lo;
+    unsigned long long* g_gain_hi;
     Globals* glob;
     const uint32_t* verts;    // bucket-ordered vertex ids
     int64_t n;
@@ -89,6 +96,21 @@ __host__ __device__ __forceinline__ uint32_t color_of(uint32_t v, int colors) {
     return x % (uint32_t)colors;
 }
 
+// 2m of vertex i's graph.
+__device__ __forceinline__ unsigned long long two_m_of(const SweepArgs& a, uint32_t i) {
+    return a.gid ? a.two_m_g[a.gid[i]] : a.glob->two_m;
+}
+
+// Per-graph statistics of a mover (batched form).
+__device__ __forceinline__ void graph_stats(const SweepArgs& a, uint32_t i, u128 gain) {
+    const uint32_t g = a.gid[i];
+    atomicAdd(&a.g_moved[g], 1ull);
+    const unsigned long long lo = (unsigned long long)gain, hi = (unsigned long long)(gain >> 64);
+    const unsigned long long old = atomicAdd(&a.g_gain_lo[g], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&a.g_gain_hi[g], hi + carry);
+}
+
 // Refine mode (Leiden): a singleton community whose vertex has the colour of
 // the deciding sub-sweep is not a candidate (its only member may leave in the
 // same sub-sweep).  Louvain: a singleton may not join a larger-id singleton.
@@ -106,10 +128,11 @@ cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, 
 // colors * nb * bucket_tiles(n) entries; bucket_starts (colors * nb + 1 int64)
 // receives the first index of every (colour, bucket) range in verts and the
 // total.  Rows of length 0 are not listed; their label is
-// copied from labels_in to labels_out when labels_out is not null.
+// copied from labels_in to labels_out when labels_out is not null.  The
+// colour class of vertex v is that of cid[v] (of v when cid is null).
 int64_t bucket_tiles(int64_t n);
 cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
-                          uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
+                          const uint32_t* cid, uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s);
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
@@ -186,7 +209,8 @@ cudaError_t launch_narrow(const unsigned long long* wsum, int64_t m, uint32_t* w
 // mlp.cu (learned skip proposal)
 cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_t* labels, const uint64_t* Sigma,
                             const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
-                            const uint8_t* since_move, const float* attach, int64_t n, void* x, cudaStream_t s);
+                            const uint8_t* since_move, const float* attach, bool attach_raw, int64_t n, void* x,
+                            cudaStream_t s);
 cudaError_t launch_mlp_forward(const void* x, int64_t n, const float* param, float* p, uint8_t* active, float thr,
                                cudaStream_t s);
 int64_t mlp_grad_blocks(int64_t n);

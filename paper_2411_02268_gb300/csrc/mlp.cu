@@ -21,7 +21,8 @@ __global__ void k_features(const int64_t* __restrict__ off, const uint64_t* __re
                            const uint32_t* __restrict__ labels, const uint64_t* __restrict__ Sigma,
                            const uint32_t* __restrict__ size, unsigned long long two_m,
                            const uint8_t* __restrict__ moved_last, const uint8_t* __restrict__ since_move,
-                           const float* __restrict__ attach, int64_t n, __half* __restrict__ x) {
+                           const float* __restrict__ attach, bool attach_raw, int64_t n,
+                           __half* __restrict__ x) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t d = labels[i];
@@ -34,7 +35,9 @@ __global__ void k_features(const int64_t* __restrict__ off, const uint64_t* __re
     f[3] = log2f(1.0f + (float)size[d]) / 24.0f;
     f[4] = two_m ? sqrtf(sd / (float)two_m) : 0.0f;
     f[5] = sd > 0.0f ? (float)K[i] / sd : 0.0f;
-    f[6] = attach ? attach[i] : 0.0f;
+    // attach: the ratio, or (attach_raw) K_{i->C_i} as the sweep kernels store it
+    const float ki = (float)K[i];
+    f[6] = !attach ? 0.0f : !attach_raw ? attach[i] : (K[i] ? attach[i] / ki : 0.0f);
     f[7] = 1.0f;
     __half2 h[4];
 #pragma unroll
@@ -222,10 +225,12 @@ __global__ void k_mark_neighbours(const int64_t* __restrict__ off, const int32_t
 
 cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_t* labels, const uint64_t* Sigma,
                             const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
-                            const uint8_t* since_move, const float* attach, int64_t n, void* x, cudaStream_t s) {
+                            const uint8_t* since_move, const float* attach, bool attach_raw, int64_t n, void* x,
+                            cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_features<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, K, labels, Sigma, size, two_m, moved_last,
-                                                           since_move, attach, n, static_cast<__half*>(x));
+                                                           since_move, attach, attach_raw, n,
+                                                           static_cast<__half*>(x));
     return cudaGetLastError();
 }
 

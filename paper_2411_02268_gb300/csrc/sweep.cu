@@ -201,7 +201,8 @@ __device__ __forceinline__ int bucket_of(int64_t deg, const BucketTable& bt) {
 }
 
 __device__ __forceinline__ int key_of(const int64_t* __restrict__ off, int64_t v, int64_t n, int64_t nnz,
-                                      const BucketTable& bt, int colors, Globals* glob) {
+                                      const BucketTable& bt, int colors, const uint32_t* __restrict__ cid,
+                                      Globals* glob) {
     int64_t o0 = off[v], o1 = off[v + 1];
     bool bad = o1 < o0 || o0 < 0 || o1 > nnz || (v == 0 && o0 != 0) || (v == n - 1 && o1 != nnz);
     if (bad) {
@@ -210,13 +211,14 @@ __device__ __forceinline__ int key_of(const int64_t* __restrict__ off, int64_t v
     }
     int b = bucket_of(o1 - o0, bt);
     if (b < 0) return -1;
-    return (int)color_of((uint32_t)v, colors) * bt.nb + b;
+    return (int)color_of(cid ? cid[v] : (uint32_t)v, colors) * bt.nb + b;
 }
 
 int64_t bucket_tiles(int64_t n) { return (n + kBucketTile - 1) / kBucketTile; }
 
 __global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt, int colors,
-                               uint32_t* __restrict__ tile_counts, int64_t ntiles, Globals* glob) {
+                               const uint32_t* __restrict__ cid, uint32_t* __restrict__ tile_counts, int64_t ntiles,
+                               Globals* glob) {
     __shared__ uint32_t cnt[kMaxKeys];
     const int nkeys = colors * bt.nb;
     cnt[threadIdx.x] = 0;
@@ -225,7 +227,7 @@ __global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64
     for (int r = 0; r < kBucketTile / 256; ++r) {
         int64_t v = base + r * 256 + threadIdx.x;
         if (v < n) {
-            int key = key_of(off, v, n, nnz, bt, colors, glob);
+            int key = key_of(off, v, n, nnz, bt, colors, cid, glob);
             if (key >= 0) atomicAdd(&cnt[key], 1u);
         }
     }
@@ -260,7 +262,8 @@ __global__ void k_scan_small(const uint32_t* __restrict__ in, uint32_t* __restri
 }
 
 __global__ void k_bucket_scatter(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt,
-                                 int colors, const uint32_t* __restrict__ tile_offsets, int64_t ntiles,
+                                 int colors, const uint32_t* __restrict__ cid,
+                                 const uint32_t* __restrict__ tile_offsets, int64_t ntiles,
                                  uint32_t* __restrict__ verts, const uint32_t* __restrict__ labels_in,
                                  uint32_t* __restrict__ labels_out) {
     __shared__ uint32_t wc[8][kMaxKeys];
@@ -275,7 +278,7 @@ __global__ void k_bucket_scatter(const int64_t* __restrict__ off, int64_t n, int
         int64_t v = base + r * 256 + threadIdx.x;
         int key = -1;
         if (v < n) {
-            key = key_of(off, v, n, nnz, bt, colors, nullptr);
+            key = key_of(off, v, n, nnz, bt, colors, cid, nullptr);
             if (key < 0 && labels_out) labels_out[v] = labels_in[v];
         }
         unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -305,16 +308,16 @@ __global__ void k_bucket_starts(const uint32_t* __restrict__ tile_offsets, int64
 }
 
 cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
-                          uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
+                          const uint32_t* cid, uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s) {
     const int nkeys = colors * bt.nb;
     if (nkeys > kMaxKeys) return cudaErrorInvalidValue;
     if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (nkeys + 1), s);
     int64_t ntiles = bucket_tiles(n);
-    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, tile_counts, ntiles, glob);
+    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_counts, ntiles, glob);
     k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, ntiles * nkeys, &glob->count);
-    k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, tile_offsets, ntiles, verts,
+    k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_offsets, ntiles, verts,
                                                       labels_in, labels_out);
     k_bucket_starts<<<1, 256, 0, s>>>(tile_offsets, ntiles, nkeys, &glob->count, bucket_starts);
     return cudaGetLastError();

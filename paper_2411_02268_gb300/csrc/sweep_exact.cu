@@ -81,7 +81,7 @@ __device__ __forceinline__ Best scan_table(const SweepArgs& a, const uint32_t* k
                                            unsigned long long kid) {
     Best best{0, kEmpty};
     const bool lpa = a.mode == CD_MODE_LPA;
-    const unsigned long long two_m = a.glob->two_m;
+    const unsigned long long two_m = two_m_of(a, i);
     const unsigned long long Ki = a.K[i];
     const unsigned long long Sd = lpa ? 0ull : a.Sigma[d];
     const bool sd1 = lpa ? false : a.size[d] == 1;
@@ -119,6 +119,7 @@ __device__ __forceinline__ void exact_epilogue(const SweepArgs& a, bool moved, u
         hi = hi + h2 + (nl < lo ? 1ull : 0ull);
         lo = nl;
     }
+    if (moved && a.gid) graph_stats(a, v, gain);
     unsigned long long base = 0;
     if (lane == 0) {
         base = atomicAdd(&a.glob->moved, (unsigned long long)__popc(mm));
@@ -133,10 +134,7 @@ __device__ __forceinline__ void exact_epilogue(const SweepArgs& a, bool moved, u
 __device__ __forceinline__ void finish(const SweepArgs& a, uint32_t i, uint32_t d, unsigned long long kid,
                                        const Best& b, unsigned long long kbest, bool& moved, u128& gain) {
     moved = b.c != kEmpty;
-    if (a.attach) {
-        const unsigned long long Ki = a.K[i];
-        a.attach[i] = Ki ? (float)(moved ? kbest : kid) / (float)Ki : 0.0f;
-    }
+    if (a.attach) a.attach[i] = (float)(moved ? kbest : kid);
     if (moved) {
         a.labels_out[i] = b.c;
         gain = a.mode == CD_MODE_LPA ? (u128)((unsigned long long)b.gain - kid) : (u128)b.gain;
@@ -167,6 +165,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_group(const SweepArgs a,
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.gdone && a.gdone[a.gid[i]]) act = false;
         if (a.bound) {
             bi = a.bound[i];
             if (a.size[d] != 1) act = false;  // refine: only singletons move
@@ -217,7 +216,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep_exact_block(const SweepArgs a,
     const int64_t start = a.off[i], end = a.off[i + 1];
     const uint32_t d = a.labels[i];
     const uint32_t bi = a.bound ? a.bound[i] : 0u;
-    const bool act = !(a.active && !a.active[i]) && !(a.bound && a.size[d] != 1);
+    const bool act = !(a.active && !a.active[i]) && !(a.bound && a.size[d] != 1) &&
+                     !(a.gdone && a.gdone[a.gid[i]]);
     uint32_t T;
     uint32_t* keys;
     unsigned long long* vals;

@@ -84,7 +84,7 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
         gain_out = have ? (u128)(bk - kid) : (u128)0;
         best_w = bk;
     } else {
-        const unsigned long long two_m = a.glob->two_m;
+        const unsigned long long two_m = two_m_of(a, i);
         const unsigned long long Ki = a.K[i];
         const unsigned long long Sd = a.Sigma[d];
         const bool sd1 = a.size[d] == 1;
@@ -101,10 +101,7 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
         gain_out = have ? (u128)bg : (u128)0;
     }
     best_out = best;
-    if (a.attach) {
-        const unsigned long long Ki = a.K[i];
-        a.attach[i] = Ki ? (float)best_w / (float)Ki : 0.0f;
-    }
+    if (a.attach) a.attach[i] = (float)best_w;
     return have;
 }
 
@@ -242,6 +239,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.gdone && a.gdone[a.gid[i]]) act = false;
         if (a.bound) {
             bi = a.bound[i];
             if (a.size[d] != 1) act = false;  // refine: only singletons move
@@ -386,6 +384,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
         end = a.off[i + 1];
         d = a.labels[i];
         if (a.active && !a.active[i]) act = false;
+        if (a.gdone && a.gdone[a.gid[i]]) act = false;
         if (a.bound) {
             bi = a.bound[i];
             if (a.size[d] != 1) act = false;  // refine: only singletons move
@@ -489,6 +488,7 @@ __device__ __forceinline__ void epilogue(const SweepArgs& a, const Outcome& o) {
         hi = hi + h2 + (nl < lo ? 1ull : 0ull);
         lo = nl;
     }
+    if (o.moved && a.gid) graph_stats(a, o.vertex, o.gain);
     unsigned long long base = 0;
     if (lane == 0) {
         base = atomicAdd(&a.glob->moved, (unsigned long long)__popc(mm));

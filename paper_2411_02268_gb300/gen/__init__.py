@@ -227,3 +227,31 @@ def rmat22(seed: int = 1) -> Graph:
 def rmat25(seed: int = 1) -> Graph:
     """R-MAT scale 25, edge factor 16, (0.57, 0.19, 0.19, 0.05), w in [1, 255]."""
     return rmat(25, 16, 0.57, 0.19, 0.19, wmax=255, seed=seed)
+
+
+def sbm_batch_params(count: int = 512, seed: int = 1, n_range=(1000, 200000), k_range=(10, 2000),
+                     d_range=(8.0, 64.0), ratio: float = 10.0):
+    """Parameters of a batch of planted-partition graphs of uneven size:
+    n log-uniform in n_range, the community count log-uniform in k_range
+    (at most n / 2), the average degree d uniform in d_range, and
+    p_in = ratio * p_out with p_out = d / (ratio (s - 1) + (n - s)) for
+    blocks of s = n / K vertices (so that the expected degree is d).
+    Returns a list of (n, K, p_in, p_out, graph_seed)."""
+    r = np.random.default_rng([int(seed), 0x5B1])
+    out = []
+    for g in range(count):
+        n = int(round(np.exp(r.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        K = int(round(np.exp(r.uniform(np.log(k_range[0]), np.log(k_range[1])))))
+        K = max(1, min(K, n // 2))
+        d = float(r.uniform(d_range[0], d_range[1]))
+        s = n / K
+        p_out = d / (ratio * (s - 1.0) + (n - s))
+        p_in = min(1.0, ratio * p_out)
+        out.append((n, K, p_in, p_out, (int(seed) << 20) + g))
+    return out
+
+
+def sbm_batch(count: int = 512, seed: int = 1, wmax: int = 16, **kw) -> list[Graph]:
+    """A batch of planted-partition graphs (see sbm_batch_params), weights
+    uniform in [1, wmax], graph g seeded by (seed, g)."""
+    return [sbm(n, K, p_in, p_out, wmax, gs) for (n, K, p_in, p_out, gs) in sbm_batch_params(count, seed, **kw)]

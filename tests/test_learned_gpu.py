@@ -104,7 +104,7 @@ def test_learned_skip_gains_over_plain(env, gname):
     planted partition) the learned proposal lets the sweeps scan far fewer
     entries than the plain method, and fewer than the "no neighbour moved"
     rule, at a modularity loss within 0.5%.  (On R-MAT graphs, where hubs
-    touch most vertices, it saves little: see the design doc.)"""
+    touch most vertices, the proposal keeps most of them and saves little.)"""
     cd, torch = env
     m, *_ = trained_model(cd, torch)
     g = gen.grid(256, 256, 0.02, 16, seed=2) if gname == "grid256" else gen.sbm(20000, 200, 0.02, 0.0002, 4, 3)
@@ -114,7 +114,7 @@ def test_learned_skip_gains_over_plain(env, gname):
     _, q_learn = cd.cd_louvain(G, cd.make_params(k=8, skip_rule=1, skip_threshold=0.02, skip_model=m))
     st = cd.cd_last_stats()
     s_learn = st.entries_scanned
-    assert st.full_sweeps >= 2            # the plain sweep is the fallback and the judge
+    assert st.full_sweeps >= 2            # the plain sweep is the fallback and decides convergence
     _, q_triv = cd.cd_louvain(G, cd.make_params(k=8, skip_rule=2))
     s_triv = cd.cd_last_stats().entries_scanned
     print(f"{gname}: plain Q={q_plain:.5f} scanned={s_plain}; learned Q={q_learn:.5f} scanned={s_learn}; "
