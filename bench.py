@@ -34,6 +34,8 @@ import numpy as np  # noqa: E402
 WORKLOADS = {
     "rmat22": dict(desc="R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
     "rmat20": dict(desc="R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
+    "rmat25": dict(desc="R-MAT scale 25, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,255], seed 1"),
+    "rmat24": dict(desc="R-MAT scale 24, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
     "sbm10k": dict(desc="planted-partition SBM 10k vertices, 100 blocks, p_in 0.05, p_out 0.0005, w=1"),
 }
 
@@ -44,6 +46,10 @@ def make_graph(name: str):
         return gen.rmat22(1)
     if name == "rmat20":
         return gen.rmat(20, 16, wmax=16, seed=1)
+    if name == "rmat25":
+        return gen.rmat25(1)
+    if name == "rmat24":
+        return gen.rmat(24, 16, wmax=16, seed=1)
     if name == "sbm10k":
         return gen.sbm_10k(1)
     raise ValueError(name)
@@ -60,13 +66,13 @@ def algorithmic_bytes(g, k: int) -> dict:
                 bytes=12 * int(g.nnz) + 36 * n_active)
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(k: int = 8) -> str:
+    """Hash of the sources that define the k-slot sweep kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_02268_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.startswith("sweep") or f == "cd_internal.cuh":
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ("cd_internal.cuh", "sweep_mg.cuh", f"sweep_k{k}.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -79,7 +85,7 @@ def ncu_traffic(workload: str, k: int):
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(k):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -175,10 +181,12 @@ def oracle_sample(g, k: int, seconds: float, threads: int):
         frac = min(1.0, frac * max(2.0, min(8.0, seconds / max(dt, 1e-3))))
 
 
-def learned_vs_plain(cd, torch, side: int):
-    """Learned skip proposal against the plain method: train on move traces
-    of small graphs, then run Louvain on a side x side grid with 2% of edges
-    rewired, w in [1, 16]."""
+def learned_vs_plain(cd, torch, side: int, rmat_scale: int = 0):
+    """Learned skip proposal against the plain method and the "no neighbour
+    moved" rule: train on move traces of small graphs, then run Louvain on a
+    side x side grid with 2% of edges rewired (w in [1, 16]) and, with
+    rmat_scale, on an R-MAT graph of that scale (edge factor 16, w in
+    [1, 16])."""
     from paper_2411_02268_gb300 import gen
     t0 = time.perf_counter()
     xs, ys = [], []
@@ -189,25 +197,34 @@ def learned_vs_plain(cd, torch, side: int):
     model = cd.MLP.init(seed=0)
     loss = cd.cd_mlp_train(torch.cat(xs), torch.cat(ys), model, steps=400, lr=0.02)
     t_train = time.perf_counter() - t0
-    g = gen.grid(side, side, 0.02, 16, seed=1)
-    G = cd.Graph.to_device(g)
-    out = {"graph": f"grid {side}x{side}, 2% rewired, w in [1,16]", "n": g.n, "nnz": g.nnz,
-           "train_samples": int(sum(len(y) for y in ys)), "train_loss": loss, "train_seconds": round(t_train, 2)}
-    for name, kw in (("plain", {}), ("learned", dict(skip_rule=1, skip_threshold=0.02, skip_model=model)),
-                     ("neighbour_rule", dict(skip_rule=2))):
-        cd.cd_louvain(G, cd.make_params(k=8, **kw))  # warm-up
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        _, q = cd.cd_louvain(G, cd.make_params(k=8, **kw))
-        torch.cuda.synchronize()
-        st = cd.cd_last_stats()
-        out[name] = {"q": q, "ms": (time.perf_counter() - t) * 1e3, "entries_scanned": int(st.entries_scanned),
-                     "sweeps": int(st.sweeps), "full_sweeps": int(st.full_sweeps)}
-    qp = out["plain"]["q"]
-    for name in ("learned", "neighbour_rule"):
-        out[name]["q_loss_pct"] = (qp - out[name]["q"]) / abs(qp) * 100 if qp else 0.0
-        out[name]["scanned_vs_plain"] = out[name]["entries_scanned"] / max(out["plain"]["entries_scanned"], 1)
-        out[name]["speedup_vs_plain"] = out["plain"]["ms"] / out[name]["ms"]
+    out = {"train_samples": int(sum(len(y) for y in ys)), "train_loss": loss, "train_seconds": round(t_train, 2)}
+    graphs = []
+    if side > 0:
+        graphs.append(("grid", f"grid {side}x{side}, 2% rewired, w in [1,16]", lambda: gen.grid(side, side, 0.02, 16, seed=1)))
+    if rmat_scale > 0:
+        graphs.append(("rmat", f"R-MAT scale {rmat_scale}, edge factor 16, w in [1,16]",
+                       lambda: gen.rmat(rmat_scale, 16, wmax=16, seed=1)))
+    for key, desc, make in graphs:
+        g = make()
+        G = cd.Graph.to_device(g)
+        r = {"graph": desc, "n": g.n, "nnz": g.nnz}
+        for name, kw in (("plain", {}), ("learned", dict(skip_rule=1, skip_threshold=0.02, skip_model=model)),
+                         ("neighbour_rule", dict(skip_rule=2))):
+            cd.cd_louvain(G, cd.make_params(k=8, **kw))  # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, q = cd.cd_louvain(G, cd.make_params(k=8, **kw))
+            torch.cuda.synchronize()
+            st = cd.cd_last_stats()
+            r[name] = {"q": q, "ms": (time.perf_counter() - t) * 1e3, "entries_scanned": int(st.entries_scanned),
+                       "sweeps": int(st.sweeps), "full_sweeps": int(st.full_sweeps)}
+        qp = r["plain"]["q"]
+        for name in ("learned", "neighbour_rule"):
+            r[name]["q_loss_pct"] = (qp - r[name]["q"]) / abs(qp) * 100 if qp else 0.0
+            r[name]["scanned_vs_plain"] = r[name]["entries_scanned"] / max(r["plain"]["entries_scanned"], 1)
+            r[name]["speedup_vs_plain"] = r["plain"]["ms"] / r[name]["ms"]
+        out[key] = r
+        del G
     return out
 
 
@@ -295,8 +312,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--learned-side", type=int, default=2048,
+    ap.add_argument("--learned-side", type=int, default=4096,
                     help="side of the rewired grid for the learned-skip comparison (0 = skip it)")
+    ap.add_argument("--learned-rmat", type=int, default=0,
+                    help="also compare the learned skip on an R-MAT graph of this scale (0 = no)")
     ap.add_argument("--warm-seconds", type=float, default=1.0,
                     help="after the warm-up steps, keep stepping (untimed) for this long")
     ap.add_argument("--batch-count", type=int, default=512,
@@ -403,8 +422,8 @@ def main():
                 "algorithmic_bytes": ab["bytes"], "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
 
     learned = None
-    if args.learned_side > 0:
-        learned = learned_vs_plain(cd, torch, args.learned_side)
+    if args.learned_side > 0 or args.learned_rmat > 0:
+        learned = learned_vs_plain(cd, torch, args.learned_side, args.learned_rmat)
     batched = None
     if args.batch_count > 0:
         batched = batched_vs_plain(cd, torch, args.batch_count)

@@ -105,7 +105,9 @@ typedef struct cd_mlp {
 } cd_mlp;
 
 typedef struct cd_params {
-    int32_t k;            /* MG slots: 1, 2, 4, 8 or 16; 0 = exact hashtable */
+    int32_t k;            /* MG slots: 1, 2, 4, 8, 16, 32 or 64; 0 = exact hashtable.  With
+                             32 or 64 slots (the paper's Leiden uses 64, Section 5.3) a
+                             schedule may give a row at most 32 streams */
     int32_t subtract;     /* 0 = conditional (Algorithm 1), 1 = unconditional (Section 4.1) */
     double tolerance;     /* Louvain: stop a pass when the sweep's summed delta-Q <= tolerance;
                              LPA: stop when at most tolerance * n labels changed (Section 3.5) */

@@ -85,7 +85,7 @@ int check_csr(const cd_csr* g) {
     return CD_OK;
 }
 
-void default_schedule(cd_schedule* s) {
+void default_schedule(int k, cd_schedule* s) {
     // Streams per row by row length: one stream up to 128 entries, then about
     // 64-256 entries per stream (the merge tree costs about k updates per
     // stream), 256 streams for the hubs; narrow length bands keep the rows
@@ -97,7 +97,9 @@ void default_schedule(cd_schedule* s) {
     std::memset(s, 0, sizeof(*s));
     s->nbuckets = nb;
     s->vec = 4;
-    for (int b = 0; b < nb; ++b) { s->deg_max[b] = dm[b]; s->lanes[b] = ln[b]; }
+    // sketches of 32 or 64 slots merge inside one warp: at most 32 streams
+    const int cap = k >= 32 ? 32 : 256;
+    for (int b = 0; b < nb; ++b) { s->deg_max[b] = dm[b]; s->lanes[b] = ln[b] < cap ? ln[b] : cap; }
 }
 
 int check_schedule(const cd_schedule* s) {
@@ -113,14 +115,21 @@ int check_schedule(const cd_schedule* s) {
 
 int check_params(const cd_params* p) {
     if (!p) return CD_EINVAL;
-    if (!(p->k == 0 || p->k == 1 || p->k == 2 || p->k == 4 || p->k == 8 || p->k == 16)) return CD_EINVAL;
+    if (!(p->k == 0 || p->k == 1 || p->k == 2 || p->k == 4 || p->k == 8 || p->k == 16 || p->k == 32 ||
+          p->k == 64))
+        return CD_EINVAL;
     if (p->subtract != 0 && p->subtract != 1) return CD_EINVAL;
     if (p->one_scan != 0 && p->one_scan != 1) return CD_EINVAL;
     if (p->one_scan && p->k == 0) return CD_EINVAL;
     if (!(p->agg_k == 0 || p->agg_k == 1 || p->agg_k == 2 || p->agg_k == 4 || p->agg_k == 8 || p->agg_k == 16))
         return CD_EINVAL;
     if (p->skip_rule < 0 || p->skip_rule > 2 || (p->skip_rule == 1 && !p->skip_model)) return CD_EINVAL;
-    if (p->sched) CD_TRY(check_schedule(p->sched));
+    if (p->sched) {
+        CD_TRY(check_schedule(p->sched));
+        if (p->k >= 32)
+            for (int b = 0; b < p->sched->nbuckets; ++b)
+                if (p->sched->lanes[b] > 32) return CD_EINVAL;
+    }
     return CD_OK;
 }
 
@@ -980,7 +989,7 @@ int cd_last_stats(cd_stats* out) {
 
 int cd_default_schedule(int k, cd_schedule* out) {
     if (!out || k < 0) return CD_EINVAL;
-    default_schedule(out);
+    default_schedule(k, out);
     return CD_OK;
 }
 
@@ -997,7 +1006,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     if (!labels_in || !labels_out || labels_in == labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     const bool host = g->memory == CD_MEM_HOST;
     if (host) {
         for (int64_t i = 0; i < g->n; ++i)
@@ -1120,7 +1129,7 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
     if (!labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     Scratch sc(s);
     Globals* dglob;
     CD_TRY(sc.get(&dglob, 1));
@@ -1178,7 +1187,7 @@ int cd_louvain_batched(const cd_csr* graphs, int ngraphs, const cd_params* p, ui
     }
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     Scratch sc(s);
     Globals* dglob;
     CD_TRY(sc.get(&dglob, 1));
@@ -1374,7 +1383,7 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
     }
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule base;
-    if (p->sched) base = *p->sched; else default_schedule(&base);
+    if (p->sched) base = *p->sched; else default_schedule(p->k, &base);
     cd_tune_report rep;
     std::memset(&rep, 0, sizeof(rep));
     std::vector<cd_schedule> tuned((size_t)nks, base);
@@ -1435,10 +1444,17 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
             HostGlobals hg;
             return read_globals(dglob, nullptr, 0, &hg, s);
         };
-        CD_TRY(time_sweep(base, ks[0], &rep.default_ms));
+        {
+            cd_schedule b0 = base;
+            if (ks[0] >= 32)
+                for (int b = 0; b < b0.nbuckets; ++b) b0.lanes[b] = std::min(b0.lanes[b], 32);
+            CD_TRY(time_sweep(b0, ks[0], &rep.default_ms));
+        }
         for (int i = 0; i < nks; ++i) {
             const int k = ks[i];
             cd_schedule cur = base;
+            const int cap = k >= 32 ? 32 : 256;
+            for (int b = 0; b < cur.nbuckets; ++b) cur.lanes[b] = std::min(cur.lanes[b], cap);
             double best = 0.0;
             CD_TRY(time_sweep(cur, k, &best));
             if (k > 0) {
@@ -1450,7 +1466,7 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
                     if (!any) continue;
                     const int l0 = cur.lanes[b];
                     for (int cand : {l0 / 2, l0 * 2}) {
-                        if (cand < 1 || cand > 256) continue;
+                        if (cand < 1 || cand > cap) continue;
                         cd_schedule t = cur;
                         t.lanes[b] = cand;
                         double ms = 0.0;
@@ -1532,7 +1548,7 @@ int cd_lpa(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double* q_
     if (!labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     Scratch sc(s);
     Globals* dglob;
     CD_TRY(sc.get(&dglob, 1));
@@ -1566,7 +1582,7 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
     if (resolve_colors(p) < 2) return CD_EINVAL;  // refinement needs two colour classes or more
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     Scratch sc(s);
     Globals* dglob;
     CD_TRY(sc.get(&dglob, 1));
@@ -1724,7 +1740,7 @@ int cd_trace(const cd_csr* g, const cd_params* p, double sample_rate, uint16_t* 
     if (g->memory != CD_MEM_DEVICE || !x_out || !y_out || capacity < 0 || !count_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
-    if (p->sched) sched = *p->sched; else default_schedule(&sched);
+    if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     Scratch sc(s);
     Globals* dglob;
     CD_TRY(sc.get(&dglob, 1));
@@ -1755,7 +1771,7 @@ int cd_aggregate_mg(const cd_csr* g, const uint32_t* labels, int k, int subtract
     if (!labels || !dense_out || !offsets_out || !n_out || !nnz_out) return CD_EINVAL;
     if (g->n > 0 && (!cols_out || !weights_out)) return CD_EINVAL;
     cd_schedule sched;
-    if (schedp) { CD_TRY(check_schedule(schedp)); sched = *schedp; } else default_schedule(&sched);
+    if (schedp) { CD_TRY(check_schedule(schedp)); sched = *schedp; } else default_schedule(k, &sched);
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
     Globals* dglob;

@@ -120,14 +120,11 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
     if (valid) {
         i = verts[vi];
         const int64_t start = off[i], end = off[i + 1];
-        if (L == 1) {
-            for (int64_t e = start; e < end; ++e) {
-                const uint32_t x = __ldg(w + e);
-                zero |= x == 0;
-                sum += x;
-            }
-        } else {
+        {
+            // 16-byte chunks, several in flight per thread (one thread per row
+            // for the short rows would otherwise wait on one 4-byte load at a time)
             const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
+#pragma unroll 4
             for (int64_t ch = c0 + lane; ch < c1; ch += L) {
                 const int64_t e0 = ch * 4;
                 uint32_t xs[4];
@@ -330,6 +327,8 @@ extern template cudaError_t launch_k<2>(const SweepArgs&, bool, int64_t, cudaStr
 extern template cudaError_t launch_k<4>(const SweepArgs&, bool, int64_t, cudaStream_t);
 extern template cudaError_t launch_k<8>(const SweepArgs&, bool, int64_t, cudaStream_t);
 extern template cudaError_t launch_k<16>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<32>(const SweepArgs&, bool, int64_t, cudaStream_t);
+extern template cudaError_t launch_k<64>(const SweepArgs&, bool, int64_t, cudaStream_t);
 template <int K>
 cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStream_t s);
 extern template cudaError_t launch_agg_k<1>(const AggArgs&, bool, int64_t, cudaStream_t);
@@ -351,12 +350,17 @@ cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, c
 
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s) {
     if (nblocks == 0) return cudaSuccess;
+    if (k >= 32)  // these sketch sizes merge inside one warp
+        for (int b = 0; b < a.bt.nb; ++b)
+            if (a.bt.lanes[b] > 32) return cudaErrorInvalidValue;
     switch (k) {
         case 1: return launch_k<1>(a, wide, nblocks, s);
         case 2: return launch_k<2>(a, wide, nblocks, s);
         case 4: return launch_k<4>(a, wide, nblocks, s);
         case 8: return launch_k<8>(a, wide, nblocks, s);
         case 16: return launch_k<16>(a, wide, nblocks, s);
+        case 32: return launch_k<32>(a, wide, nblocks, s);
+        case 64: return launch_k<64>(a, wide, nblocks, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,8 @@
+// MG-sketch sweep kernel for sketch size k = 32 (the large-sketch form: at most
+// 32 streams per row, merges and candidate tables in shared memory; MG
+// aggregation is offered up to k = 16).
+#include "sweep_mg.cuh"
+
+namespace cdk {
+template cudaError_t launch_k<32>(const SweepArgs&, bool, int64_t, cudaStream_t);
+}  // namespace cdk

@@ -7,6 +7,8 @@
 // (Appendix A.1) for the sketch update; Section 4.3 for LPA.
 #pragma once
 
+#include <type_traits>
+
 #include "cd_internal.cuh"
 
 namespace cdk {
@@ -96,6 +98,47 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
             if (barred(a, c, d, sd1)) continue;
             i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
                      (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
+            if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; best_w = acc[p]; }
+        }
+        gain_out = have ? (u128)bg : (u128)0;
+    }
+    best_out = best;
+    if (a.attach) a.attach[i] = (float)best_w;
+    return have;
+}
+
+// decide() for candidate tables in shared memory (large sketches): the same
+// rule over cand[0, K) and acc[0, K), in a loop.
+template <int K, typename VT>
+__device__ __noinline__ bool decide_dyn(const SweepArgs& a, uint32_t i, uint32_t d, const uint32_t* cand,
+                                        const VT* acc, VT kid, uint32_t& best_out, u128& gain_out) {
+    uint32_t best = d;
+    VT best_w = kid;
+    bool have = false;
+    if (a.mode == CD_MODE_LPA) {
+        VT bk = kid;
+#pragma unroll 1
+        for (int p = 0; p < K; ++p) {
+            const uint32_t c = cand[p];
+            if (c == kEmpty) continue;
+            const VT v = acc[p];
+            if (v > kid && (v > bk || (v == bk && c < best))) { best = c; bk = v; have = true; }
+        }
+        gain_out = have ? (u128)(bk - kid) : (u128)0;
+        best_w = bk;
+    } else {
+        const unsigned long long two_m = two_m_of(a, i);
+        const unsigned long long Ki = a.K[i];
+        const unsigned long long Sd = a.Sigma[d];
+        const bool sd1 = a.size[d] == 1;
+        i128 bg = 0;
+#pragma unroll 1
+        for (int p = 0; p < K; ++p) {
+            const uint32_t c = cand[p];
+            if (c == kEmpty) continue;
+            if (barred(a, c, d, sd1)) continue;
+            const i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
+                           (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
             if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; best_w = acc[p]; }
         }
         gain_out = have ? (u128)bg : (u128)0;
@@ -314,6 +357,135 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
 }
 
 // ---------------------------------------------------------------------------
+// Large sketches (k = 32, 64): G <= 32 streams per vertex inside one warp, as
+// group_body, with the merge tree and the candidate tables in a per-warp
+// shared-memory stage (the register form would unroll k x k updates per
+// merge round and hold k more values per lane).  Merge round o: streams
+// [o, 2o) of each group stage their sketch at rows wb/2 + (lane - o) (wb =
+// the group's first lane in the warp) and streams [0, o) feed them slot by
+// slot.  Then the stage holds one candidate table per group; the second
+// scan adds each entry's weight to its candidate's slot with a shared-memory
+// atomic (integer sums: order-independent).
+// ---------------------------------------------------------------------------
+template <int K, typename VT>
+struct WarpStage {
+    struct Merge {
+        uint32_t k[K][16];
+        VT v[K][16];
+        int lossy[16];
+    };
+    struct Tables {
+        uint32_t cand[32][K];
+        VT acc[32][K];
+    };
+    union {
+        Merge m;
+        Tables t;
+    };
+};
+
+template <int G, int K, typename VT>
+__device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi, bool valid,
+                                                  WarpStage<K, VT>& ws) {
+    const int lane = threadIdx.x & (G - 1);
+    const int wl = threadIdx.x & 31;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (wl & ~(G - 1)));
+    Outcome out{false, 0, 0, 0};
+    uint32_t i = 0, d = 0, bi = 0;
+    int64_t start = 0, end = 0;
+    bool act = valid;
+    if (valid) {
+        i = a.verts[vi];
+        start = a.off[i];
+        end = a.off[i + 1];
+        d = a.labels[i];
+        if (a.active && !a.active[i]) act = false;
+        if (a.gdone && a.gdone[a.gid[i]]) act = false;
+        if (a.bound) {
+            bi = a.bound[i];
+            if (a.size[d] != 1) act = false;
+        }
+    }
+    Sketch<K, VT> sk;
+    sk.init();
+    const bool unc = a.uncond != 0;
+    const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
+    const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
+    if (act) scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+    const int wb = wl & ~(G - 1);
+#pragma unroll 1
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        if (lane >= o && lane < 2 * o) {
+            const int r = wb / 2 + (lane - o);
+#pragma unroll
+            for (int p = 0; p < K; ++p) {
+                ws.m.k[p][r] = sk.key[p];
+                ws.m.v[p][r] = sk.value(p);
+            }
+            ws.m.lossy[r] = sk.lossy;
+        }
+        __syncwarp(gmask);
+        if (lane < o) {
+            const int r = wb / 2 + lane;
+#pragma unroll 1
+            for (int p = 0; p < K; ++p) {
+                const VT v = ws.m.v[p][r];
+                if (v > 0) sk.update(ws.m.k[p][r], v, unc);
+            }
+            sk.lossy |= ws.m.lossy[r] != 0;
+        }
+        __syncwarp(gmask);
+    }
+    __syncwarp();  // every group of the warp has merged: the stage becomes the candidate tables
+    uint32_t* cs = ws.t.cand[wl / G];
+    VT* as = ws.t.acc[wl / G];
+    const bool exact = __shfl_sync(gmask, (int)sk.lossy, 0, G) == 0 || a.one_scan;
+    VT kid = 0;
+    if (lane == 0) {
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            const VT v = sk.value(p);
+            const uint32_t kk = v > 0 ? sk.key[p] : kEmpty;
+            cs[p] = kk == d ? kEmpty : kk;
+            as[p] = (exact && kk != d) ? v : (VT)0;  // exact when the sketch never subtracted
+            kid += kk == d ? v : (VT)0;
+        }
+    }
+    __syncwarp(gmask);
+    if (!exact) {
+        kid = 0;
+        uint32_t cand[K];
+#pragma unroll
+        for (int p = 0; p < K; ++p) cand[p] = cs[p];
+        if (act) {
+            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) {
+                kid += c == d ? (VT)w : (VT)0;
+                int m = -1;
+#pragma unroll
+                for (int p = 0; p < K; ++p) m = c == cand[p] ? p : m;
+                if (m >= 0) atomicAdd(&as[m], (VT)w);
+            });
+        }
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) kid += __shfl_down_sync(gmask, kid, o, G);
+        __syncwarp(gmask);
+    }
+    if (act && lane == 0) {
+        uint32_t best;
+        u128 g;
+        const bool mv = decide_dyn<K, VT>(a, i, d, cs, as, kid, best, g);
+        a.labels_out[i] = best;
+        out.moved = mv;
+        out.gain = g;
+        out.vertex = i;
+        out.scanned = (uint32_t)(end - start);
+    } else if (valid && !act && lane == 0) {
+        a.labels_out[i] = d;
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
 // L = 64, 128 or 256 streams per vertex: L/32 warps (a sub-block of the
 // 256-thread block, synchronised by a named barrier).
 // ---------------------------------------------------------------------------
@@ -471,38 +643,75 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     return out;
 }
 
-// Warp-level statistics and mover list; every lane of the warp must call it.
-__device__ __forceinline__ void epilogue(const SweepArgs& a, const Outcome& o) {
+// Block totals of the epilogue: movers, their 128-bit gain, entries scanned,
+// and the block's first slot in the mover list.
+struct EpiSmem {
+    unsigned cnt;
+    unsigned long long lo, hi, scanned, base;
+};
+
+// Block-level statistics and mover list: warp sums go to shared memory and
+// one thread adds the block's totals to the globals (one set of global
+// atomics per block instead of per warp).  Every thread of the block must
+// call it.
+__device__ __forceinline__ void block_epilogue(const SweepArgs& a, const Outcome& o, EpiSmem& e) {
     const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) { e.cnt = 0; e.lo = 0; e.hi = 0; e.scanned = 0; }
+    __syncthreads();
     const unsigned sc = __reduce_add_sync(0xffffffffu, o.scanned);
-    if (lane == 0 && sc) atomicAdd(&a.glob->scanned, (unsigned long long)sc);
-    unsigned mm = __ballot_sync(0xffffffffu, o.moved);
-    if (mm == 0) return;
-    unsigned long long lo = o.moved ? (unsigned long long)o.gain : 0ull;
-    unsigned long long hi = o.moved ? (unsigned long long)(o.gain >> 64) : 0ull;
+    const unsigned mm = __ballot_sync(0xffffffffu, o.moved);
+    unsigned woff = 0;
+    if (mm) {
+        unsigned long long lo = o.moved ? (unsigned long long)o.gain : 0ull;
+        unsigned long long hi = o.moved ? (unsigned long long)(o.gain >> 64) : 0ull;
 #pragma unroll
-    for (int q = 16; q >= 1; q >>= 1) {
-        unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, q);
-        unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, q);
-        unsigned long long nl = lo + l2;
-        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-        lo = nl;
+        for (int q = 16; q >= 1; q >>= 1) {
+            unsigned long long l2 = __shfl_down_sync(0xffffffffu, lo, q);
+            unsigned long long h2 = __shfl_down_sync(0xffffffffu, hi, q);
+            unsigned long long nl = lo + l2;
+            hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+            lo = nl;
+        }
+        if (lane == 0) {
+            woff = atomicAdd(&e.cnt, (unsigned)__popc(mm));
+            unsigned long long old = atomicAdd(&e.lo, lo);
+            hi += (old + lo < old) ? 1ull : 0ull;
+            if (hi) atomicAdd(&e.hi, hi);
+        }
+        woff = __shfl_sync(0xffffffffu, woff, 0);
+        if (o.moved && a.gid) graph_stats(a, o.vertex, o.gain);
     }
-    if (o.moved && a.gid) graph_stats(a, o.vertex, o.gain);
-    unsigned long long base = 0;
-    if (lane == 0) {
-        base = atomicAdd(&a.glob->moved, (unsigned long long)__popc(mm));
-        unsigned long long old = atomicAdd(&a.glob->gain_lo, lo);
-        unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-        if (hi + carry) atomicAdd(&a.glob->gain_hi, hi + carry);
+    if (lane == 0 && sc) atomicAdd(&e.scanned, (unsigned long long)sc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (e.scanned) atomicAdd(&a.glob->scanned, e.scanned);
+        if (e.cnt) {
+            e.base = atomicAdd(&a.glob->moved, (unsigned long long)e.cnt);
+            unsigned long long old = atomicAdd(&a.glob->gain_lo, e.lo);
+            unsigned long long carry = (old + e.lo < old) ? 1ull : 0ull;
+            if (e.hi + carry) atomicAdd(&a.glob->gain_hi, e.hi + carry);
+        }
     }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (o.moved && a.movers) a.movers[base + __popc(mm & ((1u << lane) - 1u))] = o.vertex;
+    __syncthreads();
+    if (o.moved && a.movers) a.movers[e.base + woff + __popc(mm & ((1u << lane) - 1u))] = o.vertex;
+}
+
+// Shared memory of the sub-block merges (k <= 16; larger sketches use at
+// most 32 streams per row and merge inside one warp).
+struct NoSmem {};
+template <int K, typename VT>
+using SweepSmem = typename std::conditional<(K <= 16), BlockSmem<K, VT>, NoSmem>::type;
+
+template <int K, typename VT>
+constexpr int sweep_min_blocks() {
+    return K >= 32 ? 1 : ((K >= 16 || sizeof(VT) == 8) ? 2 : 4);
 }
 
 template <int K, typename VT>
-__global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) k_sweep_mg(const SweepArgs a) {
-    __shared__ BlockSmem<K, VT> sm;
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(const SweepArgs a) {
+    __shared__ SweepSmem<K, VT> sm;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];  // k >= 32: one WarpStage per warp
+    __shared__ EpiSmem esm;
     // blocks of the longest rows first, so that they start at once and
     // overlap with the many short rows instead of trailing the launch
     const int64_t blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
@@ -516,18 +725,30 @@ __global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) 
     const int64_t vi = a.bt.vbegin[b] + lb * vpb + threadIdx.x / L;
     const bool valid = vi < a.bt.vbegin[b + 1];
     Outcome o;
-    switch (L) {
-        case 1: o = group_body<1, K, VT>(a, vi, valid); break;
-        case 2: o = group_body<2, K, VT>(a, vi, valid); break;
-        case 4: o = group_body<4, K, VT>(a, vi, valid); break;
-        case 8: o = group_body<8, K, VT>(a, vi, valid); break;
-        case 16: o = group_body<16, K, VT>(a, vi, valid); break;
-        case 32: o = group_body<32, K, VT>(a, vi, valid); break;
-        case 64: o = block_body<64, K, VT>(a, vi, valid, sm); break;
-        case 128: o = block_body<128, K, VT>(a, vi, valid, sm); break;
-        default: o = block_body<256, K, VT>(a, vi, valid, sm); break;
+    if constexpr (K >= 32) {
+        WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
+        switch (L) {  // the host caps L at 32 for these sketch sizes
+            case 1: o = group_body_big<1, K, VT>(a, vi, valid, ws); break;
+            case 2: o = group_body_big<2, K, VT>(a, vi, valid, ws); break;
+            case 4: o = group_body_big<4, K, VT>(a, vi, valid, ws); break;
+            case 8: o = group_body_big<8, K, VT>(a, vi, valid, ws); break;
+            case 16: o = group_body_big<16, K, VT>(a, vi, valid, ws); break;
+            default: o = group_body_big<32, K, VT>(a, vi, valid, ws); break;
+        }
+    } else {
+        switch (L) {
+            case 1: o = group_body<1, K, VT>(a, vi, valid); break;
+            case 2: o = group_body<2, K, VT>(a, vi, valid); break;
+            case 4: o = group_body<4, K, VT>(a, vi, valid); break;
+            case 8: o = group_body<8, K, VT>(a, vi, valid); break;
+            case 16: o = group_body<16, K, VT>(a, vi, valid); break;
+            case 32: o = group_body<32, K, VT>(a, vi, valid); break;
+            case 64: o = block_body<64, K, VT>(a, vi, valid, sm); break;
+            case 128: o = block_body<128, K, VT>(a, vi, valid, sm); break;
+            default: o = block_body<256, K, VT>(a, vi, valid, sm); break;
+        }
     }
-    epilogue(a, o);
+    block_epilogue(a, o, esm);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,11 +851,22 @@ cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStrea
     return cudaGetLastError();
 }
 
+template <int K, typename VT>
+cudaError_t launch_k_vt(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
+    size_t dyn = 0;
+    if constexpr (K >= 32) {
+        dyn = sizeof(WarpStage<K, VT>) * (kBlock / 32);
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_mg<K, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
+    k_sweep_mg<K, VT><<<(unsigned)nblocks, kBlock, dyn, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_k(const SweepArgs& a, bool wide, int64_t nblocks, cudaStream_t s) {
-    if (wide) k_sweep_mg<K, unsigned long long><<<(unsigned)nblocks, kBlock, 0, s>>>(a);
-    else k_sweep_mg<K, uint32_t><<<(unsigned)nblocks, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    if (wide) return launch_k_vt<K, unsigned long long>(a, nblocks, s);
+    return launch_k_vt<K, uint32_t>(a, nblocks, s);
 }
 
 }  // namespace cdk

@@ -137,7 +137,7 @@ def test_degenerate_driver_inputs(env):
 
 
 @pytest.mark.parametrize("gname", list(GRAPHS))
-@pytest.mark.parametrize("k", [8, 0, 16])
+@pytest.mark.parametrize("k", [8, 0, 16, 64])
 def test_leiden_bit_exact_with_twin(env, gname, k):
     cd, torch = env
     g = GRAPHS[gname]()

@@ -273,7 +273,7 @@ def test_repeatable(env):
 
 
 @pytest.mark.parametrize("gname", ["sbm10k", "rmat12_w16", "ragged_loops", "grid_rewired"])
-@pytest.mark.parametrize("k", [8, 16, 0])
+@pytest.mark.parametrize("k", [8, 16, 0, 64])
 def test_refine_sub_sweep_parity(env, gname, k):
     """One refine-mode sub-sweep (Leiden, Section 3.4): bound filter, the
     singleton-only rule and the same-colour singleton bar, per colour class,
@@ -306,7 +306,7 @@ def test_refine_sub_sweep_parity(env, gname, k):
 
 
 @pytest.mark.parametrize("gname", list(GRAPHS))
-@pytest.mark.parametrize("k", [1, 8])
+@pytest.mark.parametrize("k", [1, 8, 32])
 def test_lpa_one_scan_parity(env, gname, k):
     """LPA 1-scan (Section 4.3): decisions on the sketch values alone."""
     cd, torch = env
@@ -319,3 +319,54 @@ def test_lpa_one_scan_parity(env, gname, k):
         ref, gains = oracle.sweep(g, lab, oracle.MODE_LPA, k, False, osched, threads=4, one_scan=True)
         assert np.array_equal(out.cpu().numpy().view(np.uint32), ref)
         assert gain == oracle.gain_total(gains)
+
+
+# ---- large sketches (k = 32, 64: the paper's Leiden uses 64 slots) --------------------
+# These merge inside one warp, so their schedules give a row at most 32 streams.
+BIG_LANES = ([1, 2, 4, 8, 16, 40, 2**62], [1, 2, 4, 8, 16, 32, 32])
+BIG_NARROW = ([2**62], [8])
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("k", [32, 64])
+def test_large_sketch_default_schedule(env, gname, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    assert max(cd.cd_default_schedule(k).as_lists()[1]) <= 32
+    for _, lab in label_states(g, 6):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k)
+
+
+@pytest.mark.parametrize("gname", ["rmat12_w16", "ragged_loops", "sbm10k", "rmat11_w255_perm"])
+@pytest.mark.parametrize("sched_name", ["big_lanes", "narrow"])
+@pytest.mark.parametrize("k", [32, 64])
+def test_large_sketch_stream_schedules(env, gname, sched_name, k):
+    cd, torch = env
+    g = GRAPHS[gname]()
+    s = sched_for(cd, k, *{"big_lanes": BIG_LANES, "narrow": BIG_NARROW}[sched_name])
+    for _, lab in label_states(g, 7):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, sched=s)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, uncond=1, sched=s)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k, sched=s)
+
+
+@pytest.mark.parametrize("k", [32, 64])
+def test_large_sketch_wide_values(env, k):
+    """Rows whose weighted degree needs 64-bit sketch values."""
+    cd, torch = env
+    base = gen.rmat(10, 16, wmax=16, seed=8)
+    w = (base.w.astype(np.uint64) * (2**27)).astype(np.uint32)  # up to 2^31
+    g = gen.Graph(base.n, base.offsets, base.cols, w, "rmat10_heavy")
+    assert int(np.max(np.add.reduceat(g.w.astype(np.uint64), g.offsets[:-1][np.diff(g.offsets) > 0]))) >= 2**32
+    for _, lab in label_states(g, 8):
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k)
+
+
+def test_large_sketch_rejects_wide_streams(env):
+    cd, torch = env
+    g = GRAPHS["rmat12_w16"]()
+    s = sched_for(cd, 64, *WIDE)
+    with pytest.raises(cd.CDError):
+        gpu_sweep(cd, torch, g, np.arange(g.n, dtype=np.uint32), oracle.MODE_LOUVAIN, 64, sched=s)
