@@ -228,6 +228,33 @@ def learned_vs_plain(cd, torch, side: int, rmat_scale: int = 0):
     return out
 
 
+def variants_vs_exact(cd, torch, G):
+    """The paper's comparison (Section 5.2-5.4) on the bench graph: each
+    method with its MG sketch size against the exact hashtable (k = 0) and
+    weighted Boyer-Moore (k = 1): modularity, wall time of the whole
+    detection (device-resident graph) and peak device scratch."""
+    runs = [("louvain", 8, {}), ("louvain", 1, {}), ("louvain", 0, {}),
+            ("leiden", 64, {}), ("leiden", 8, {}), ("leiden", 0, {}),
+            ("lpa", 8, {}), ("lpa", 8, {"one_scan": True}), ("lpa", 0, {})]
+    out = {}
+    for method, k, kw in runs:
+        fn = {"louvain": cd.cd_louvain, "leiden": cd.cd_leiden, "lpa": cd.cd_lpa}[method]
+        p = cd.make_params(k=k, **kw)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, q = fn(G, p)
+        torch.cuda.synchronize()
+        st = cd.cd_last_stats()
+        name = f"{method}_k{k}" + ("_1scan" if kw.get("one_scan") else "")
+        out[name] = {"q": q, "ms": (time.perf_counter() - t) * 1e3, "sweeps": int(st.sweeps),
+                     "passes": int(st.passes), "scratch_bytes": int(st.scratch_bytes)}
+    for method, k in (("louvain", 8), ("louvain", 1), ("leiden", 64), ("leiden", 8), ("lpa", 8)):
+        a, b = out[f"{method}_k{k}"], out[f"{method}_k0"]
+        a["q_vs_exact"] = a["q"] / b["q"] if b["q"] else None
+        a["time_vs_exact"] = a["ms"] / b["ms"]
+    return out
+
+
 def batched_vs_plain(cd, torch, count: int):
     """Batched Louvain against the plain method run graph by graph, on a batch
     of `count` planted-partition graphs of uneven size (n log-uniform in
@@ -316,6 +343,8 @@ def main():
                     help="side of the rewired grid for the learned-skip comparison (0 = skip it)")
     ap.add_argument("--learned-rmat", type=int, default=0,
                     help="also compare the learned skip on an R-MAT graph of this scale (0 = no)")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="1 = also run Louvain/Leiden/LPA with their sketch sizes against the exact hashtable")
     ap.add_argument("--warm-seconds", type=float, default=1.0,
                     help="after the warm-up steps, keep stepping (untimed) for this long")
     ap.add_argument("--batch-count", type=int, default=512,
@@ -427,6 +456,7 @@ def main():
     batched = None
     if args.batch_count > 0:
         batched = batched_vs_plain(cd, torch, args.batch_count)
+    variants = variants_vs_exact(cd, torch, G) if args.variants else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,6 +476,7 @@ def main():
                        "gen_seconds": round(t_gen, 2)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "learned_vs_plain": learned,
             "batched_vs_plain": batched,
+            "variants_vs_exact": variants,
             "gpu_launches": 7 * args.steps, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -98,10 +98,38 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
     }
 }
 
-// K_i = sum of w over row i for the rows listed in the bucket table: rows of
-// bucket b are summed by lanes[b] threads (one thread per row for the short
-// rows), with 16-byte loads and a shuffle reduction; each row's sum is written
-// once (rows of length 0 are not listed and keep K = 0).
+// K_i = sum of w over row i for the rows listed in the bucket table.  Rows of
+// a bucket with L <= 32 streams are summed by L threads of a warp (one thread
+// per row for the short rows), rows of the wider buckets by a whole block;
+// 16-byte loads, four of them in flight per thread (the long rows are
+// otherwise latency-bound), then a shuffle (and shared-memory) reduction.
+// Each row's sum is written once; rows of length 0 are not listed and keep
+// K = 0.
+__device__ __forceinline__ uint4 load_w4(const uint32_t* __restrict__ w, int64_t ch, int64_t nnz) {
+    const int64_t e0 = ch * 4;
+    if (e0 + 4 <= nnz) return __ldg(reinterpret_cast<const uint4*>(w) + ch);
+    uint4 v;
+    v.x = e0 < nnz ? w[e0] : 0u;
+    v.y = e0 + 1 < nnz ? w[e0 + 1] : 0u;
+    v.z = e0 + 2 < nnz ? w[e0 + 2] : 0u;
+    v.w = e0 + 3 < nnz ? w[e0 + 3] : 0u;
+    return v;
+}
+
+__device__ __forceinline__ void add_w4(uint4 v, int64_t ch, int64_t start, int64_t end, unsigned long long& sum,
+                                       bool& zero) {
+    const int64_t e0 = ch * 4;
+    const uint32_t xs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool in = e0 + u >= start && e0 + u < end;
+        zero |= in && xs[u] == 0;
+        sum += in ? xs[u] : 0u;
+    }
+}
+
+__device__ __forceinline__ int row_sum_lanes(int lanes) { return lanes <= 32 ? lanes : kBlock; }
+
 __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ off, const uint32_t* __restrict__ w,
                                                   int64_t nnz, const uint32_t* __restrict__ verts, BucketTable bt,
                                                   unsigned long long* __restrict__ K, Globals* glob) {
@@ -110,8 +138,8 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
 #pragma unroll
     for (int q = 1; q < CD_MAX_BUCKETS; ++q)
         if (q < bt.nb && blk >= bt.bbegin[q]) b = q;
-    const int L = bt.lanes[b] < 32 ? bt.lanes[b] : 32;  // at most a warp per row
-    const int64_t vi = bt.vbegin[b] + (blk - bt.bbegin[b]) * (256 / L) + threadIdx.x / L;
+    const int L = row_sum_lanes(bt.lanes[b]);
+    const int64_t vi = bt.vbegin[b] + (blk - bt.bbegin[b]) * (kBlock / L) + threadIdx.x / L;
     const bool valid = vi < bt.vbegin[b + 1];
     const int lane = threadIdx.x % L;
     unsigned long long sum = 0;
@@ -120,33 +148,32 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
     if (valid) {
         i = verts[vi];
         const int64_t start = off[i], end = off[i + 1];
-        {
-            // 16-byte chunks, several in flight per thread (one thread per row
-            // for the short rows would otherwise wait on one 4-byte load at a time)
-            const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
-#pragma unroll 4
-            for (int64_t ch = c0 + lane; ch < c1; ch += L) {
-                const int64_t e0 = ch * 4;
-                uint32_t xs[4];
-                if (e0 + 4 <= nnz) {
-                    const uint4 v = __ldg(reinterpret_cast<const uint4*>(w) + ch);
-                    xs[0] = v.x; xs[1] = v.y; xs[2] = v.z; xs[3] = v.w;
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) xs[u] = e0 + u < nnz ? w[e0 + u] : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const bool in = e0 + u >= start && e0 + u < end;
-                    zero |= in && xs[u] == 0;
-                    sum += in ? xs[u] : 0u;
-                }
-            }
+        const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
+        int64_t ch = c0 + lane;
+        for (; ch + 3 * (int64_t)L < c1; ch += 4 * (int64_t)L) {
+            const uint4 v0 = load_w4(w, ch, nnz);
+            const uint4 v1 = load_w4(w, ch + L, nnz);
+            const uint4 v2 = load_w4(w, ch + 2 * L, nnz);
+            const uint4 v3 = load_w4(w, ch + 3 * L, nnz);
+            add_w4(v0, ch, start, end, sum, zero);
+            add_w4(v1, ch + L, start, end, sum, zero);
+            add_w4(v2, ch + 2 * L, start, end, sum, zero);
+            add_w4(v3, ch + 3 * L, start, end, sum, zero);
         }
+        for (; ch < c1; ch += L) add_w4(load_w4(w, ch, nnz), ch, start, end, sum, zero);
     }
     if (L > 1) {
-        const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
-        for (int o = L / 2; o >= 1; o >>= 1) sum += __shfl_down_sync(gmask, sum, o, L);
+        const int G = L < 32 ? L : 32;
+        const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+        for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_down_sync(gmask, sum, o, G);
+    }
+    if (L == kBlock) {
+        __shared__ unsigned long long part[kBlock / 32];
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < kBlock / 32; ++q) sum += part[q];
+        }
     }
     if (valid && lane == 0) K[i] = sum;
     if (zero) atomicOr(&glob->err, kErrZeroWeight);
@@ -154,19 +181,19 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
 
 cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
                             const BucketTable& bt_in, uint64_t* K, Globals* glob, cudaStream_t s) {
-    // geometry: min(lanes, 32) threads per row, 256-thread blocks
+    // geometry: L <= 32 threads per row, or a block per row for wider buckets
     BucketTable bt = bt_in;
     int64_t blk = 0;
     for (int b = 0; b < bt.nb; ++b) {
         bt.bbegin[b] = blk;
-        const int L = bt.lanes[b] < 32 ? bt.lanes[b] : 32;
+        const int L = bt.lanes[b] <= 32 ? bt.lanes[b] : kBlock;
         const int64_t nv = bt.vbegin[b + 1] - bt.vbegin[b];
-        blk += (nv + (256 / L) - 1) / (256 / L);
+        blk += (nv + (kBlock / L) - 1) / (kBlock / L);
     }
     bt.bbegin[bt.nb] = blk;
     (void)n;
     if (blk == 0) return cudaSuccess;
-    k_row_sums<<<(unsigned)blk, 256, 0, s>>>(off, w, nnz, verts, bt, (unsigned long long*)K, glob);
+    k_row_sums<<<(unsigned)blk, kBlock, 0, s>>>(off, w, nnz, verts, bt, (unsigned long long*)K, glob);
     return cudaGetLastError();
 }
 
