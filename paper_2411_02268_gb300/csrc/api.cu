@@ -2,6 +2,7 @@
 // scratch, the launch sequence of one sweep, modularity, and host-memory
 // staging.  Every entry point returns a status code and never aborts.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -39,13 +40,32 @@ int cuda_fail(cudaError_t e) {
         if (_rc != CD_OK) return _rc; \
     } while (0)
 
+// The device's default memory pool (which cudaMallocAsync draws from) keeps up
+// to kPoolKeep bytes of freed scratch between calls instead of returning it
+// to the driver at every synchronisation: calls that allocate the same
+// scratch again (every sweep of a benchmark, every host-memory call) then
+// reuse mapped memory.  Set once per device, for this process only.
+constexpr uint64_t kPoolKeep = 16ull << 30;
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_pool_set[kMaxDevices];
+
+void keep_pool_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    if (g_pool_set[dev].exchange(1) != 0) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t keep = kPoolKeep;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
 // Stream-ordered device scratch of one call; everything is released (in stream
 // order) when the object goes out of scope.
 struct Scratch {
     cudaStream_t s;
     std::vector<void*> ptrs;
     int64_t bytes = 0;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    explicit Scratch(cudaStream_t st) : s(st) { keep_pool_memory(); }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, s);
         if (bytes > g_stats.scratch_bytes) g_stats.scratch_bytes = bytes;
@@ -665,13 +685,13 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     uint32_t *tflags = nullptr, *tpos = nullptr;
     unsigned long long* ttiles = nullptr;
     if (rule == 1 || trace) {
-        uint16_t* xh;
-        CD_TRY(sc.get(&xh, L.n * 8));
-        x = xh;
         CD_TRY(sc.get(&attach, L.n));
         CD_CUDA(cudaMemsetAsync(attach, 0, sizeof(float) * L.n, s));
     }
     if (trace) {
+        uint16_t* xh;  // feature rows of the traced sweeps
+        CD_TRY(sc.get(&xh, L.n * 8));
+        x = xh;
         CD_TRY(sc.get(&tflags, L.n));
         CD_TRY(sc.get(&tpos, L.n));
         CD_TRY(sc.get(&ttiles, scan_tiles(L.n) + 1));
@@ -727,37 +747,45 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
                                           p->max_sweeps, B->gsweeps, B->gdone, dglob, st));
         return CD_OK;
     };
-    Replay rp;
-    if (p->capture && !track && !p->timing && sweep_is_async(L, p->k)) {
-        // record one sweep on a private stream; replays go to s
-        CD_CUDA(cudaStreamCreateWithFlags(&rp.cs, cudaStreamNonBlocking));
-        CD_CUDA(cudaStreamBeginCapture(rp.cs, cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue(rp.cs, false);
-        cudaGraph_t gr = nullptr;
-        const cudaError_t ec = cudaStreamEndCapture(rp.cs, &gr);
-        rp.graph = gr;
-        CD_TRY(rc);
-        CD_CUDA(ec);
-        CD_CUDA(cudaGraphInstantiate(&rp.exec, rp.graph, 0));
+    // one sweep: the skip proposal (masked sweeps), the sub-sweeps, the move state
+    auto sweep_seq = [&](cudaStream_t st, bool use_mask) -> int {
+        if (use_mask && rule == 2) {
+            // movers of the previous sweep and their neighbours
+            CD_CUDA(cudaMemsetAsync(active, 0, L.n, st));
+            CD_CUDA(launch_mark_neighbours(L.off, L.cols, L.movers, dglob, active, st));
+        }
+        if (use_mask && rule == 1)
+            CD_CUDA(launch_propose(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, L.n,
+                                   param, p->skip_threshold, active, st));
+        if (track) CD_CUDA(cudaMemcpyAsync(before, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, st));
+        CD_TRY(enqueue(st, use_mask));
+        if (track) CD_CUDA(launch_move_state(before, la, L.n, moved_last, since_move, st));
+        return CD_OK;
+    };
+    // full and masked sweeps recorded once each as CUDA graphs (replayed on s)
+    Replay rp[2];
+    if (p->capture && !trace && !p->timing && sweep_is_async(L, p->k)) {
+        for (int m = 0; m < (rule != 0 ? 2 : 1); ++m) {
+            CD_CUDA(cudaStreamCreateWithFlags(&rp[m].cs, cudaStreamNonBlocking));
+            CD_CUDA(cudaStreamBeginCapture(rp[m].cs, cudaStreamCaptureModeThreadLocal));
+            const int rc = sweep_seq(rp[m].cs, m == 1);
+            cudaGraph_t gr = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(rp[m].cs, &gr);
+            rp[m].graph = gr;
+            CD_TRY(rc);
+            CD_CUDA(ec);
+            CD_CUDA(cudaGraphInstantiate(&rp[m].exec, rp[m].graph, 0));
+        }
     }
     int64_t sw = 0;
     bool force_full = false;
     for (; sw < p->max_sweeps;) {
         const bool use_mask = rule != 0 && sw > 0 && !force_full;
-        if (use_mask && rule == 2) {
-            // movers of the previous sweep and their neighbours
-            CD_CUDA(cudaMemsetAsync(active, 0, L.n, s));
-            CD_CUDA(launch_mark_neighbours(L.off, L.cols, L.movers, dglob, active, s));
-        }
-        if ((use_mask && rule == 1) || (trace && sw > 0)) {
+        if (trace && sw > 0)
             CD_CUDA(launch_features(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, true,
                                     L.n, x, s));
-            if (use_mask) CD_CUDA(launch_mlp_forward(x, L.n, param, nullptr, active, p->skip_threshold, s));
-        }
-        if (track) CD_CUDA(cudaMemcpyAsync(before, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
-        if (rp.exec) CD_CUDA(cudaGraphLaunch(rp.exec, s));
-        else CD_TRY(enqueue(s, use_mask));
-        if (track) CD_CUDA(launch_move_state(before, la, L.n, moved_last, since_move, s));
+        if (rp[use_mask ? 1 : 0].exec) CD_CUDA(cudaGraphLaunch(rp[use_mask ? 1 : 0].exec, s));
+        else CD_TRY(sweep_seq(s, use_mask));
         HostGlobals hg;
         if (trace && sw > 0) {
             const double r = trace->rate < 0 ? 0 : (trace->rate > 1 ? 1 : trace->rate);

@@ -211,6 +211,12 @@ cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_
                             const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
                             const uint8_t* since_move, const float* attach, bool attach_raw, int64_t n, void* x,
                             cudaStream_t s);
+// Features and forward pass in one kernel (attach holds raw K_{i->C_i}):
+// active[i] = (predicted move probability >= thr).
+cudaError_t launch_propose(const int64_t* off, const uint64_t* K, const uint32_t* labels, const uint64_t* Sigma,
+                           const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
+                           const uint8_t* since_move, const float* attach, int64_t n, const float* param, float thr,
+                           uint8_t* active, cudaStream_t s);
 cudaError_t launch_mlp_forward(const void* x, int64_t n, const float* param, float* p, uint8_t* active, float thr,
                                cudaStream_t s);
 int64_t mlp_grad_blocks(int64_t n);

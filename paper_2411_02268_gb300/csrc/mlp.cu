@@ -17,14 +17,12 @@ namespace cdk {
 //   3 log2(1 + |community|) / 24       4 sqrt(Sigma_d / 2m)
 //   5 K_i / Sigma_d                     6 K_{i->C_i} / K_i at the vertex's last
 //   decision (0 before it)              7 1
-__global__ void k_features(const int64_t* __restrict__ off, const uint64_t* __restrict__ K,
-                           const uint32_t* __restrict__ labels, const uint64_t* __restrict__ Sigma,
-                           const uint32_t* __restrict__ size, unsigned long long two_m,
-                           const uint8_t* __restrict__ moved_last, const uint8_t* __restrict__ since_move,
-                           const float* __restrict__ attach, bool attach_raw, int64_t n,
-                           __half* __restrict__ x) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ uint4 vertex_features(int64_t i, const int64_t* __restrict__ off,
+                                                 const uint64_t* __restrict__ K, const uint32_t* __restrict__ labels,
+                                                 const uint64_t* __restrict__ Sigma, const uint32_t* __restrict__ size,
+                                                 unsigned long long two_m, const uint8_t* __restrict__ moved_last,
+                                                 const uint8_t* __restrict__ since_move,
+                                                 const float* __restrict__ attach, bool attach_raw) {
     const uint32_t d = labels[i];
     const float deg = (float)(off[i + 1] - off[i]);
     const float sd = (float)Sigma[d];
@@ -39,15 +37,27 @@ __global__ void k_features(const int64_t* __restrict__ off, const uint64_t* __re
     const float ki = (float)K[i];
     f[6] = !attach ? 0.0f : !attach_raw ? attach[i] : (K[i] ? attach[i] / ki : 0.0f);
     f[7] = 1.0f;
-    __half2 h[4];
+    uint4 raw;
+    __half2* h = reinterpret_cast<__half2*>(&raw);
 #pragma unroll
     for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(f[2 * q], f[2 * q + 1]);
-    *reinterpret_cast<uint4*>(x + i * 8) = *reinterpret_cast<uint4*>(h);
+    return raw;
 }
 
-__device__ __forceinline__ float mlp_logit(const __half* __restrict__ xrow, const float* W1, const float* b1,
-                                           const float* w2, float b2, float* h_out) {
-    const uint4 raw = *reinterpret_cast<const uint4*>(xrow);
+__global__ void k_features(const int64_t* __restrict__ off, const uint64_t* __restrict__ K,
+                           const uint32_t* __restrict__ labels, const uint64_t* __restrict__ Sigma,
+                           const uint32_t* __restrict__ size, unsigned long long two_m,
+                           const uint8_t* __restrict__ moved_last, const uint8_t* __restrict__ since_move,
+                           const float* __restrict__ attach, bool attach_raw, int64_t n,
+                           __half* __restrict__ x) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    *reinterpret_cast<uint4*>(x + i * 8) =
+        vertex_features(i, off, K, labels, Sigma, size, two_m, moved_last, since_move, attach, attach_raw);
+}
+
+__device__ __forceinline__ float mlp_logit_raw(const uint4 raw, const float* W1, const float* b1, const float* w2,
+                                               float b2, float* h_out) {
     const __half2* hx = reinterpret_cast<const __half2*>(&raw);
     float x[8];
 #pragma unroll
@@ -67,6 +77,11 @@ __device__ __forceinline__ float mlp_logit(const __half* __restrict__ xrow, cons
         z = fmaf(w2[j], a, z);
     }
     return z;
+}
+
+__device__ __forceinline__ float mlp_logit(const __half* __restrict__ xrow, const float* W1, const float* b1,
+                                           const float* w2, float b2, float* h_out) {
+    return mlp_logit_raw(*reinterpret_cast<const uint4*>(xrow), W1, b1, w2, b2, h_out);
 }
 
 // Parameters (float32 master, device): W1 [0, 256), b1 [256, 288), w2 [288, 320),
@@ -96,6 +111,25 @@ __global__ void k_mlp_forward(const __half* __restrict__ x, int64_t n, const flo
     const float pi = 1.0f / (1.0f + expf(-z));
     if (p) p[i] = pi;
     if (active) active[i] = pi >= thr ? 1 : 0;
+}
+
+// The driver's skip proposal in one pass: the features of k_features and the
+// forward pass of k_mlp_forward on them (same float16 rounding and float32
+// arithmetic, so the same mask), without the feature rows in memory.
+__global__ void k_propose(const int64_t* __restrict__ off, const uint64_t* __restrict__ K,
+                          const uint32_t* __restrict__ labels, const uint64_t* __restrict__ Sigma,
+                          const uint32_t* __restrict__ size, unsigned long long two_m,
+                          const uint8_t* __restrict__ moved_last, const uint8_t* __restrict__ since_move,
+                          const float* __restrict__ attach, int64_t n, const float* __restrict__ param, float thr,
+                          uint8_t* __restrict__ active) {
+    __shared__ float W1[256], b1[32], w2[32], b2;
+    load_weights(param, W1, b1, w2, &b2);
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 raw = vertex_features(i, off, K, labels, Sigma, size, two_m, moved_last, since_move, attach, true);
+    const float z = mlp_logit_raw(raw, W1, b1, w2, b2, nullptr);
+    const float pi = 1.0f / (1.0f + expf(-z));
+    active[i] = pi >= thr ? 1 : 0;
 }
 
 // Per-block partial gradients of sum_i BCE(p_i, y_i) (321 floats per block,
@@ -231,6 +265,16 @@ cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_
     k_features<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, K, labels, Sigma, size, two_m, moved_last,
                                                            since_move, attach, attach_raw, n,
                                                            static_cast<__half*>(x));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propose(const int64_t* off, const uint64_t* K, const uint32_t* labels, const uint64_t* Sigma,
+                           const uint32_t* size, unsigned long long two_m, const uint8_t* moved_last,
+                           const uint8_t* since_move, const float* attach, int64_t n, const float* param, float thr,
+                           uint8_t* active, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_propose<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, K, labels, Sigma, size, two_m, moved_last, since_move,
+                                                          attach, n, param, thr, active);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,11 @@ struct Sketch {
 
     __device__ __forceinline__ VT value(int p) const { return t[p]; }
 
+    // Algorithm 1 for one (c, w): add w to the slot holding c (a slot whose
+    // value fell to 0 keeps its key and revives); otherwise (unconditional:
+    // after subtracting w from every slot) put c into the largest-index empty
+    // slot (value 0), found by a downward search; with no empty slot
+    // (conditional) subtract w from every slot, clamping at 0.
     __device__ __forceinline__ void update(uint32_t c, VT w, bool uncond) {
         bool has = false;
 #pragma unroll
@@ -46,20 +51,20 @@ struct Sketch {
         if (!has) {
             if (uncond) {
 #pragma unroll
-                for (int p = 0; p < K; ++p) t[p] = t[p] > w ? t[p] - w : (VT)0;
+                for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
                 lossy = true;
             }
-            int e = -1;
+            bool done = false;
 #pragma unroll
-            for (int p = 0; p < K; ++p)
-                if (t[p] == 0) e = p;
-            if (e >= 0) {
+            for (int p = K - 1; p >= 0; --p) {
+                const bool z = !done && t[p] == 0;
+                key[p] = z ? c : key[p];
+                t[p] = z ? w : t[p];
+                done |= z;
+            }
+            if (!done && !uncond) {
 #pragma unroll
-                for (int p = 0; p < K; ++p)
-                    if (p == e) { key[p] = c; t[p] = w; }
-            } else if (!uncond) {
-#pragma unroll
-                for (int p = 0; p < K; ++p) t[p] = t[p] > w ? t[p] - w : (VT)0;
+                for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
                 lossy = true;
             }
         }
@@ -176,7 +181,8 @@ __device__ __forceinline__ Chunk load_chunk(const SweepArgs& a, int64_t ch) {
 // Scans the chunks first, first + step, ... < c1 of the row [start, end) and
 // calls f(label of col, w) for entries inside the row that are not self-loops
 // (in refine mode only for neighbours inside the vertex's bound), in order.
-// One copy of f per chunk: the entries are shifted through slot 0.
+// Two copies of f per chunk: entries 0 and 1, then 2 and 3 shifted down
+// (four copies cost registers, one copy costs shifts; two measured fastest).
 template <typename F>
 __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, int64_t c1, int step,
                                             int64_t start, int64_t end, uint32_t i, uint32_t bi, F&& f) {
@@ -200,11 +206,12 @@ __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, i
                 if (ok[u]) ok[u] = __ldg(a.bound + cur.c[u]) == bi;
         }
 #pragma unroll 1
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             if (ok[0]) f(labs[0], cur.w[0]);
-            ok[0] = ok[1]; ok[1] = ok[2]; ok[2] = ok[3];
-            labs[0] = labs[1]; labs[1] = labs[2]; labs[2] = labs[3];
-            cur.w[0] = cur.w[1]; cur.w[1] = cur.w[2]; cur.w[2] = cur.w[3];
+            if (ok[1]) f(labs[1], cur.w[1]);
+            ok[0] = ok[2]; ok[1] = ok[3];
+            labs[0] = labs[2]; labs[1] = labs[3];
+            cur.w[0] = cur.w[2]; cur.w[1] = cur.w[3];
         }
     }
 }

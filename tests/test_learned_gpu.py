@@ -136,3 +136,19 @@ def test_skip_rules_keep_labels_valid(env):
         u = np.unique(l)
         assert u[0] == 0 and u[-1] == len(u) - 1
         assert q == pytest.approx(float(oracle.modularity_fraction(g, l)), abs=1e-15)
+
+
+def test_skip_rules_same_with_graph_replay(env):
+    """The skip sweeps replayed from CUDA graphs (fused proposal kernel) give
+    the labels of the launch-by-launch path."""
+    cd, torch = env
+    g = gen.grid(120, 120, 0.02, 16, seed=5)
+    G = cd.Graph.to_device(g)
+    m = cd.MLP.init(seed=2)
+    for rule in (1, 2):
+        outs = []
+        for capture in (True, False):
+            lab, q = cd.cd_louvain(G, cd.make_params(k=8, skip_rule=rule, skip_threshold=0.05, skip_model=m,
+                                                     capture=capture))
+            outs.append((lab.cpu().numpy(), q, cd.cd_last_stats().entries_scanned))
+        assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
