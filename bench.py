@@ -181,6 +181,30 @@ def oracle_sample(g, k: int, seconds: float, threads: int):
         frac = min(1.0, frac * max(2.0, min(8.0, seconds / max(dt, 1e-3))))
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of the ranks' values (the slowest rank's time); the value
+    itself with one process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def lpt_shards(sizes, world: int):
+    """Longest-processing-time assignment of items to `world` ranks: items in
+    descending size (ties by index) each go to the least-loaded rank (ties to
+    the lower rank).  Returns one ascending index list per rank."""
+    loads = [0] * world
+    shards = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda j: (-sizes[j], j)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        loads[r] += sizes[i]
+        shards[r].append(i)
+    return [sorted(x) for x in shards]
+
+
 def learned_vs_plain(cd, torch, side: int, rmat_scale: int = 0):
     """Learned skip proposal against the plain method and the "no neighbour
     moved" rule: train on move traces of small graphs, then run Louvain on a
@@ -255,31 +279,51 @@ def variants_vs_exact(cd, torch, G):
     return out
 
 
-def batched_vs_plain(cd, torch, count: int):
+def batched_vs_plain(cd, torch, count: int, dist=None, rank: int = 0, world: int = 1):
     """Batched Louvain against the plain method run graph by graph, on a batch
     of `count` planted-partition graphs of uneven size (n log-uniform in
     [1k, 200k], 10..2000 communities, average degree 8..64, p_in = 10 p_out,
     w in [1, 16]).  Throughput = CSR entries of all graphs / wall time of the
-    whole detection (all passes), device-resident inputs."""
+    whole detection (all passes), device-resident inputs.  With several
+    ranks the graphs are shared out by LPT on their CSR entries (no data
+    exchange: the graphs are independent) and the time is the slowest
+    rank's."""
     from paper_2411_02268_gb300 import gen
     t0 = time.perf_counter()
-    gs = gen.sbm_batch(count, seed=1)
+    params = gen.sbm_batch_params(count, seed=1)
+    # expected CSR entries of each graph (n times its expected degree), known
+    # before generating it: every rank generates only its own graphs
+    sizes = [n * (p_in * (n / k - 1) + p_out * (n - n / k)) for (n, k, p_in, p_out, _s) in params]
+    mine = lpt_shards(sizes, world)[rank]
+    gs = [gen.sbm(params[i][0], params[i][1], params[i][2], params[i][3], 16, params[i][4]) for i in mine]
     t_gen = time.perf_counter() - t0
     dev = [cd.Graph.to_device(g) for g in gs]
-    M = sum(g.nnz for g in gs)
-    N = sum(g.n for g in gs)
+    M_local = sum(g.nnz for g in gs)
+    N_local = sum(g.n for g in gs)
+    device = f"cuda:{torch.cuda.current_device()}"
+    if dist is not None:
+        tt = torch.tensor([M_local, N_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt)
+        M, N = int(tt[0].item()), int(tt[1].item())
+    else:
+        M, N = M_local, N_local
     p = cd.make_params(k=8)
-    cd.cd_louvain_batched(dev[:16], p)  # warm-up
-    for G in dev[:16]:
-        cd.cd_louvain(G, p)
+    if dev:
+        cd.cd_louvain_batched(dev[:16], p)  # warm-up
+        for G in dev[:16]:
+            cd.cd_louvain(G, p)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t = time.perf_counter()
-    labs, qb, swb = cd.cd_louvain_batched(dev, p)
+    labs, qb, swb = cd.cd_louvain_batched(dev, p) if dev else ([], np.zeros(0), np.zeros(0))
     torch.cuda.synchronize()
-    tb = time.perf_counter() - t
+    tb = max_over_ranks(time.perf_counter() - t, dist, device)
     st = cd.cd_last_stats()
     union = {"sweeps": int(st.sweeps), "passes": int(st.passes), "scratch_bytes": int(st.scratch_bytes)}
     qp, swp, same = [], [], 0
+    if dist is not None:
+        dist.barrier()
     t = time.perf_counter()
     outs = []
     for G in dev:
@@ -288,20 +332,34 @@ def batched_vs_plain(cd, torch, count: int):
         swp.append(cd.cd_last_stats().sweeps)
         outs.append(lab)
     torch.cuda.synchronize()
-    tp = time.perf_counter() - t
+    tp = max_over_ranks(time.perf_counter() - t, dist, device)
     for a, b in zip(labs, outs):
         same += bool(torch.equal(a, b))
     qb, qp = np.asarray(qb), np.asarray(qp)
+    if dist is not None:
+        tt = torch.tensor([same, float(qb.sum()), float(qp.sum()), float(np.max(np.abs(qb - qp), initial=0.0)),
+                           float(np.array_equal(np.asarray(swb), np.asarray(swp)))], dtype=torch.float64,
+                          device=device)
+        mx = tt.clone()
+        dist.all_reduce(tt)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        same, qbs, qps = int(tt[0].item()), float(tt[1].item()), float(tt[2].item())
+        maxdq, sw_same = float(mx[3].item()), bool(tt[4].item() == world)
+    else:
+        qbs, qps = float(qb.sum()), float(qp.sum())
+        maxdq = float(np.max(np.abs(qb - qp), initial=0.0))
+        sw_same = bool(np.array_equal(np.asarray(swb), np.asarray(swp)))
+    qbm, qpm = qbs / count, qps / count
     return {
-        "graphs": count, "n_total": N, "nnz_total": M, "gen_seconds": round(t_gen, 1),
-        "batched": {"ms": tb * 1e3, "gteps": M / tb / 1e9, "q_mean": float(qb.mean()), "union": union},
-        "plain_per_graph": {"ms": tp * 1e3, "gteps": M / tp / 1e9, "q_mean": float(qp.mean()),
-                            "sweeps_total": int(sum(swp))},
+        "graphs": count, "n_total": N, "nnz_total": M, "gen_seconds": round(t_gen, 1), "ranks": world,
+        "sharding": "LPT on expected CSR entries" if world > 1 else "none",
+        "batched": {"ms": tb * 1e3, "gteps": M / tb / 1e9, "q_mean": qbm, "union_rank0": union},
+        "plain_per_graph": {"ms": tp * 1e3, "gteps": M / tp / 1e9, "q_mean": qpm},
         "speedup_vs_plain": tp / tb,
-        "q_loss_pct": float((qp.mean() - qb.mean()) / abs(qp.mean()) * 100) if qp.mean() else 0.0,
-        "max_abs_dq": float(np.max(np.abs(qb - qp))),
-        "graphs_identical": int(same),
-        "sweeps_identical": bool(np.array_equal(np.asarray(swb), np.asarray(swp))),
+        "q_loss_pct": float((qpm - qbm) / abs(qpm) * 100) if qpm else 0.0,
+        "max_abs_dq": maxdq,
+        "graphs_identical": same,
+        "sweeps_identical": sw_same,
     }
 
 
@@ -411,11 +469,7 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, f"cuda:{local}")
     ms_step = ms / args.steps
     gteps = g.nnz * args.steps * world / (ms * 1e-3) / 1e9
     scratch = cd.cd_last_stats().scratch_bytes
@@ -455,7 +509,7 @@ def main():
         learned = learned_vs_plain(cd, torch, args.learned_side, args.learned_rmat)
     batched = None
     if args.batch_count > 0:
-        batched = batched_vs_plain(cd, torch, args.batch_count)
+        batched = batched_vs_plain(cd, torch, args.batch_count, dist, rank, world)
     variants = variants_vs_exact(cd, torch, G) if args.variants else None
 
     cpu = None

@@ -290,6 +290,7 @@ SweepArgs make_args(const Level& L, const uint32_t* labels_in, uint32_t* labels_
     a.glob = dglob; a.verts = L.verts; a.n = L.n; a.nnz = L.nnz; a.mode = mode; a.uncond = uncond;
     a.colors = colors; a.sub_color = sub_color;
     a.one_scan = 0;
+    a.out_all = 1;
     a.bt = L.bt;
     return a;
 }
@@ -728,6 +729,7 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
             SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract);
             a.one_scan = p->one_scan;
             a.attach = attach;
+            a.out_all = 0;  // k_commit reads the movers' entries of lb only
             if (B) {
                 a.gid = B->gid;
                 a.two_m_g = B->two_m_g;
@@ -740,7 +742,6 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
             CD_TRY(launch_sweep(Lc, a, p->k, sc, st));
             if (tms[c].on) CD_CUDA(cudaEventRecord(tms[c].b, st));
             CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, st));
-            CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, st));
         }
         if (B)
             CD_CUDA(launch_batch_converge(G, B->two_m_g, B->gstat, B->gstat + (G + 1), B->gstat + 2 * (G + 1), tol,
@@ -858,9 +859,9 @@ int refine_level(Level& L, const cd_params* p, const uint32_t* bound, const cd_s
         Level Lc = L;
         Lc.bt = L.table_for(c);
         SweepArgs a = make_args(Lc, la, lb, nullptr, bound, dglob, CD_MODE_REFINE, p->subtract, colors, c);
+        a.out_all = 0;
         CD_TRY(launch_sweep(Lc, a, p->k, sc, s));
         CD_CUDA(launch_commit(L.movers, la, lb, L.K, L.n, L.Sigma, L.size, dglob, s));
-        CD_CUDA(launch_copy_movers(L.movers, lb, la, dglob, L.n, s));
     }
     HostGlobals hg;
     CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));

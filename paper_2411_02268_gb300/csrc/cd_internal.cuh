@@ -68,6 +68,8 @@ struct SweepArgs {
     int mode;
     int uncond;
     int one_scan;             // LPA: decide on sketch values, no second scan
+    int out_all;              // 1: labels_out for every listed vertex; 0: only for the deciding ones
+                              // (the drivers read labels_out of movers only)
     int colors;               // refine: colour classes of the driver
     int sub_color;            // refine: colour class deciding in this sub-sweep
     BucketTable bt;
@@ -94,6 +96,14 @@ __host__ __device__ __forceinline__ uint32_t color_of(uint32_t v, int colors) {
     x *= 0x846ca68bU;
     x ^= x >> 16;
     return x % (uint32_t)colors;
+}
+
+// Whether vertex i decides in this sweep (the skip mask and, batched, its
+// graph still moving).
+__device__ __forceinline__ bool vertex_decides(const SweepArgs& a, uint32_t i) {
+    if (a.active && !a.active[i]) return false;
+    if (a.gdone && a.gdone[a.gid[i]]) return false;
+    return true;
 }
 
 // 2m of vertex i's graph.
@@ -140,11 +150,10 @@ cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblock
 cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
                             const BucketTable& bt, uint64_t* K, Globals* glob, cudaStream_t s);
 cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, cudaStream_t s);
-cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in,
-                          const uint32_t* labels_out, const uint64_t* K, int64_t n,
-                          uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s);
-cudaError_t launch_copy_movers(const uint32_t* movers, const uint32_t* out, uint32_t* state, Globals* glob,
-                               int64_t n, cudaStream_t s);
+// Movers [mark, moved) of the last sub-sweep: Sigma and sizes moved from
+// labels[i] to labels_out[i], then labels[i] = labels_out[i].
+cudaError_t launch_commit(const uint32_t* movers, uint32_t* labels, const uint32_t* labels_out, const uint64_t* K,
+                          int64_t n, uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s);
 
 // sweep_exact.cu
 size_t exact_group_smem(int G, uint32_t T);

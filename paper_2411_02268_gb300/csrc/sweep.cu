@@ -393,55 +393,37 @@ cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblock
 }
 
 // ---------------------------------------------------------------------------
-// Commit: apply the moves of the last sweep to Sigma and sizes (after every
-// decision of the sweep has been taken from the sweep-start state).
+// Commit: apply the moves of the last (sub-)sweep to Sigma and sizes (after
+// every decision of it has been taken from its start state), and copy the
+// movers' new labels into the running labels for the next sub-sweep.  Each
+// mover reads its old label and then overwrites it itself, so one kernel
+// does both.
 // ---------------------------------------------------------------------------
-__global__ void k_commit(const uint32_t* __restrict__ movers, const uint32_t* __restrict__ labels_in,
+__global__ void k_commit(const uint32_t* __restrict__ movers, uint32_t* __restrict__ labels,
                          const uint32_t* __restrict__ labels_out, const unsigned long long* __restrict__ K,
                          unsigned long long* __restrict__ Sigma, uint32_t* __restrict__ size,
                          const Globals* __restrict__ glob) {
     const unsigned long long cnt = glob->moved;
     for (unsigned long long t = glob->mark + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
          t += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t i = movers[t];
-        uint32_t d = labels_in[i], c = labels_out[i];
-        unsigned long long k = K[i];
+        const uint32_t i = movers[t];
+        const uint32_t d = labels[i], c = labels_out[i];
+        const unsigned long long k = K[i];
         atomicAdd(&Sigma[c], k);
         atomicAdd(&Sigma[d], ~k + 1ull);
         atomicAdd(&size[c], 1u);
         atomicSub(&size[d], 1u);
+        labels[i] = c;
     }
 }
 
-cudaError_t launch_commit(const uint32_t* movers, const uint32_t* labels_in, const uint32_t* labels_out,
-                          const uint64_t* K, int64_t n, uint64_t* Sigma, uint32_t* size, Globals* glob,
-                          cudaStream_t s) {
+cudaError_t launch_commit(const uint32_t* movers, uint32_t* labels, const uint32_t* labels_out, const uint64_t* K,
+                          int64_t n, uint64_t* Sigma, uint32_t* size, Globals* glob, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_commit<<<(unsigned)blocks, 256, 0, s>>>(movers, labels_in, labels_out,
-                                              (const unsigned long long*)K,
+    k_commit<<<(unsigned)blocks, 256, 0, s>>>(movers, labels, labels_out, (const unsigned long long*)K,
                                               (unsigned long long*)Sigma, size, glob);
-    return cudaGetLastError();
-}
-
-// state[i] = out[i] for the movers of the current sub-sweep ([mark, moved)).
-__global__ void k_copy_movers(const uint32_t* __restrict__ movers, const uint32_t* __restrict__ out,
-                              uint32_t* __restrict__ state, const Globals* __restrict__ glob) {
-    const unsigned long long cnt = glob->moved;
-    for (unsigned long long t = glob->mark + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < cnt;
-         t += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t i = movers[t];
-        state[i] = out[i];
-    }
-}
-
-cudaError_t launch_copy_movers(const uint32_t* movers, const uint32_t* out, uint32_t* state, Globals* glob,
-                               int64_t n, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_copy_movers<<<(unsigned)blocks, 256, 0, s>>>(movers, out, state, glob);
     return cudaGetLastError();
 }
 

@@ -285,14 +285,15 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     bool act = valid;
     if (valid) {
         i = a.verts[vi];
-        start = a.off[i];
-        end = a.off[i + 1];
-        d = a.labels[i];
-        if (a.active && !a.active[i]) act = false;
-        if (a.gdone && a.gdone[a.gid[i]]) act = false;
-        if (a.bound) {
-            bi = a.bound[i];
-            if (a.size[d] != 1) act = false;  // refine: only singletons move
+        act = vertex_decides(a, i);
+        if (act || a.out_all) d = a.labels[i];
+        if (act) {
+            start = a.off[i];
+            end = a.off[i + 1];
+            if (a.bound) {
+                bi = a.bound[i];
+                if (a.size[d] != 1) act = false;  // refine: only singletons move
+            }
         }
     }
     Sketch<K, VT> sk;
@@ -357,7 +358,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         out.gain = g;
         out.vertex = i;
         out.scanned = (uint32_t)(end - start);
-    } else if (valid && !act && lane == 0) {
+    } else if (valid && !act && lane == 0 && a.out_all) {
         a.labels_out[i] = d;
     }
     return out;
@@ -403,14 +404,15 @@ __device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi
     bool act = valid;
     if (valid) {
         i = a.verts[vi];
-        start = a.off[i];
-        end = a.off[i + 1];
-        d = a.labels[i];
-        if (a.active && !a.active[i]) act = false;
-        if (a.gdone && a.gdone[a.gid[i]]) act = false;
-        if (a.bound) {
-            bi = a.bound[i];
-            if (a.size[d] != 1) act = false;
+        act = vertex_decides(a, i);
+        if (act || a.out_all) d = a.labels[i];
+        if (act) {
+            start = a.off[i];
+            end = a.off[i + 1];
+            if (a.bound) {
+                bi = a.bound[i];
+                if (a.size[d] != 1) act = false;
+            }
         }
     }
     Sketch<K, VT> sk;
@@ -486,7 +488,7 @@ __device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi
         out.gain = g;
         out.vertex = i;
         out.scanned = (uint32_t)(end - start);
-    } else if (valid && !act && lane == 0) {
+    } else if (valid && !act && lane == 0 && a.out_all) {
         a.labels_out[i] = d;
     }
     return out;
@@ -559,14 +561,15 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     bool act = valid;
     if (valid) {
         i = a.verts[vi];
-        start = a.off[i];
-        end = a.off[i + 1];
-        d = a.labels[i];
-        if (a.active && !a.active[i]) act = false;
-        if (a.gdone && a.gdone[a.gid[i]]) act = false;
-        if (a.bound) {
-            bi = a.bound[i];
-            if (a.size[d] != 1) act = false;  // refine: only singletons move
+        act = vertex_decides(a, i);
+        if (act || a.out_all) d = a.labels[i];
+        if (act) {
+            start = a.off[i];
+            end = a.off[i + 1];
+            if (a.bound) {
+                bi = a.bound[i];
+                if (a.size[d] != 1) act = false;  // refine: only singletons move
+            }
         }
     }
     Sketch<K, VT> sk;
@@ -642,7 +645,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
             out.gain = g;
             out.vertex = i;
             out.scanned = (uint32_t)(end - start);
-        } else if (valid) {
+        } else if (valid && a.out_all) {
             a.labels_out[i] = d;
         }
     }
