@@ -698,6 +698,21 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         CD_TRY(sc.get(&ttiles, scan_tiles(L.n) + 1));
     }
     if (rule == 1) CD_TRY(stage_model(p->skip_model, sc, &param, s));
+    // skip sweeps of the MG kernels run over the compacted list of deciding
+    // vertices (device-side ranges), so the skipped ones cost no blocks
+    const bool compact = rule != 0 && p->k > 0;
+    const int64_t n_listed = L.starts.empty() ? 0 : L.starts.back();
+    uint32_t *cflags = nullptr, *cpos = nullptr, *cverts = nullptr;
+    unsigned long long *ctiles = nullptr, *ctotal = nullptr;
+    DevRanges* cdr = nullptr;
+    if (compact) {
+        CD_TRY(sc.get(&cflags, n_listed));
+        CD_TRY(sc.get(&cpos, n_listed));
+        CD_TRY(sc.get(&cverts, n_listed));
+        CD_TRY(sc.get(&ctiles, scan_tiles(n_listed) + 1));
+        CD_TRY(sc.get(&ctotal, 1));
+        CD_TRY(sc.get(&cdr, colors));
+    }
     const int G = B ? B->G : 0;
     if (B) {
         CD_CUDA(launch_graph_two_m(L.K, B->vb, B->nv, G, B->two_m_g, s));
@@ -730,6 +745,10 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
             a.one_scan = p->one_scan;
             a.attach = attach;
             a.out_all = 0;  // k_commit reads the movers' entries of lb only
+            if (use_mask && compact) {
+                a.verts = cverts;
+                a.dr = cdr + c;
+            }
             if (B) {
                 a.gid = B->gid;
                 a.two_m_g = B->two_m_g;
@@ -758,6 +777,9 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         if (use_mask && rule == 1)
             CD_CUDA(launch_propose(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, L.n,
                                    param, p->skip_threshold, active, st));
+        if (use_mask && compact)
+            CD_CUDA(launch_compact(L.verts, n_listed, active, L.dstarts, L.bt, colors, cflags, cpos, ctiles, ctotal,
+                                   cverts, cdr, st));
         if (track) CD_CUDA(cudaMemcpyAsync(before, la, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, st));
         CD_TRY(enqueue(st, use_mask));
         if (track) CD_CUDA(launch_move_state(before, la, L.n, moved_last, since_move, st));

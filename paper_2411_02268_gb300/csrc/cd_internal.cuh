@@ -41,6 +41,13 @@ struct BucketTable {
     int64_t bbegin[CD_MAX_BUCKETS + 1];
 };
 
+// Bucket ranges of one colour class after the skip mask has removed the
+// vertices that do not decide (written on the device, see launch_compact).
+struct DevRanges {
+    int64_t vbegin[CD_MAX_BUCKETS + 1];
+    int64_t bbegin[CD_MAX_BUCKETS + 1];
+};
+
 struct SweepArgs {
     const int64_t* off;
     const int32_t* cols;
@@ -63,6 +70,7 @@ struct SweepArgs {
     unsigned long long* g_gain_hi;
     Globals* glob;
     const uint32_t* verts;    // bucket-ordered vertex ids
+    const DevRanges* dr;      // MG sweeps: ranges of verts on the device (blocks past them exit); null = bt
     int64_t n;
     int64_t nnz;
     int mode;
@@ -146,6 +154,15 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
                           Globals* glob, cudaStream_t s);
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
+// Compaction of the bucketed vertex list to the vertices whose active byte is
+// set, order kept: cverts (n_listed), per colour class the new ranges in
+// dr[colors].  starts: the (colour, bucket) range starts of verts on the
+// device (colors * bt.nb + 1); flags/pos: n_listed scratch; tiles: scan
+// scratch; total: one device counter.
+cudaError_t launch_compact(const uint32_t* verts, int64_t n_listed, const uint8_t* active, const int64_t* starts,
+                           const BucketTable& bt, int colors, uint32_t* flags, uint32_t* pos,
+                           unsigned long long* tiles, unsigned long long* total, uint32_t* cverts, DevRanges* dr,
+                           cudaStream_t s);
 // K_i for the rows of one bucket table (vbegin ranges; bbegin is recomputed).
 cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
                             const BucketTable& bt, uint64_t* K, Globals* glob, cudaStream_t s);

@@ -393,6 +393,61 @@ cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblock
 }
 
 // ---------------------------------------------------------------------------
+// Compaction of the bucketed vertex list to the deciding vertices (skip
+// sweeps): flags, exclusive scan, scatter, and per colour class the new
+// (bucket range, block range) table, all on the device.
+// ---------------------------------------------------------------------------
+__global__ void k_active_flags(const uint32_t* __restrict__ verts, int64_t m, const uint8_t* __restrict__ active,
+                               uint32_t* __restrict__ flags) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < m) flags[j] = active[verts[j]] ? 1u : 0u;
+}
+
+__global__ void k_active_scatter(const uint32_t* __restrict__ verts, int64_t m, const uint32_t* __restrict__ flags,
+                                 const uint32_t* __restrict__ pos, uint32_t* __restrict__ cverts) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < m && flags[j]) cverts[pos[j]] = verts[j];
+}
+
+__global__ void k_active_ranges(const int64_t* __restrict__ starts, int64_t m, const uint32_t* __restrict__ pos,
+                                const unsigned long long* __restrict__ total, BucketTable bt, int colors,
+                                DevRanges* __restrict__ dr) {
+    const int c = threadIdx.x;
+    if (c >= colors) return;
+    auto at = [&](int64_t j) -> int64_t { return j < m ? (int64_t)pos[j] : (int64_t)*total; };
+    int64_t blk = 0;
+    for (int b = 0; b < bt.nb; ++b) {
+        const int64_t v0 = at(starts[(int64_t)c * bt.nb + b]), v1 = at(starts[(int64_t)c * bt.nb + b + 1]);
+        dr[c].vbegin[b] = v0;
+        dr[c].bbegin[b] = blk;
+        const int L = bt.lanes[b];
+        const int vpb = L >= kBlock ? 1 : kBlock / L;
+        blk += (v1 - v0 + vpb - 1) / vpb;
+    }
+    dr[c].vbegin[bt.nb] = at(starts[(int64_t)c * bt.nb + bt.nb]);
+    dr[c].bbegin[bt.nb] = blk;
+}
+
+cudaError_t launch_compact(const uint32_t* verts, int64_t m, const uint8_t* active, const int64_t* starts,
+                           const BucketTable& bt, int colors, uint32_t* flags, uint32_t* pos,
+                           unsigned long long* tiles, unsigned long long* total, uint32_t* cverts, DevRanges* dr,
+                           cudaStream_t s) {
+    if (colors < 1 || colors > 32) return cudaErrorInvalidValue;
+    if (m > 0) {
+        const unsigned g = (unsigned)((m + 255) / 256);
+        k_active_flags<<<g, 256, 0, s>>>(verts, m, active, flags);
+        cudaError_t e = launch_exclusive_scan_u32(flags, pos, m, tiles, total, s);
+        if (e != cudaSuccess) return e;
+        k_active_scatter<<<g, 256, 0, s>>>(verts, m, flags, pos, cverts);
+    } else {
+        cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_active_ranges<<<1, 32, 0, s>>>(starts, m, pos, total, bt, colors, dr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Commit: apply the moves of the last (sub-)sweep to Sigma and sizes (after
 // every decision of it has been taken from its start state), and copy the
 // movers' new labels into the running labels for the next sub-sweep.  Each

@@ -724,16 +724,35 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(
     __shared__ EpiSmem esm;
     // blocks of the longest rows first, so that they start at once and
     // overlap with the many short rows instead of trailing the launch
-    const int64_t blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
+    int64_t blk;
     int b = 0;
+    int64_t vb0, vb1, bb0;
+    if (a.dr) {
+        // compacted list: the grid covers the full list, blocks past the
+        // compacted one leave at once (the whole block: no barrier is reached)
+        const int64_t total = a.dr->bbegin[a.bt.nb];
+        if ((int64_t)blockIdx.x >= total) return;
+        blk = total - 1 - (int64_t)blockIdx.x;
 #pragma unroll
-    for (int q = 1; q < CD_MAX_BUCKETS; ++q)
-        if (q < a.bt.nb && blk >= a.bt.bbegin[q]) b = q;
+        for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+            if (q < a.bt.nb && blk >= a.dr->bbegin[q]) b = q;
+        bb0 = a.dr->bbegin[b];
+        vb0 = a.dr->vbegin[b];
+        vb1 = a.dr->vbegin[b + 1];
+    } else {
+        blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
+#pragma unroll
+        for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+            if (q < a.bt.nb && blk >= a.bt.bbegin[q]) b = q;
+        bb0 = a.bt.bbegin[b];
+        vb0 = a.bt.vbegin[b];
+        vb1 = a.bt.vbegin[b + 1];
+    }
     const int L = a.bt.lanes[b];
-    const int64_t lb = blk - a.bt.bbegin[b];
+    const int64_t lb = blk - bb0;
     const int vpb = L >= kBlock ? 1 : kBlock / L;
-    const int64_t vi = a.bt.vbegin[b] + lb * vpb + threadIdx.x / L;
-    const bool valid = vi < a.bt.vbegin[b + 1];
+    const int64_t vi = vb0 + lb * vpb + threadIdx.x / L;
+    const bool valid = vi < vb1;
     Outcome o;
     if constexpr (K >= 32) {
         WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
