@@ -11,6 +11,7 @@
 #include <utility>
 
 #include "cd_internal.cuh"
+#include "csr_walk.cuh"
 
 namespace cdk {
 
@@ -88,34 +89,23 @@ cudaError_t launch_scatter_bound(const uint32_t* sub, const uint32_t* bound, int
 
 // ---- super-vertex graph ----------------------------------------------------------
 
-constexpr int kExpandChunk = 64;
+constexpr int64_t kWalkTile = 4096;  // CSR entries per warp
 
-// src[e] = dense[row(e)], dst[e] = dense[cols[e]]; rows found by binary search
-// at the start of each 64-entry chunk.
+// src[e] = dense[row(e)], dst[e] = dense[cols[e]]: one warp per 4096-entry
+// tile, coalesced (csr_walk.cuh).
 __global__ void k_expand(const int64_t* __restrict__ off, const int32_t* __restrict__ cols, int64_t n,
                          int64_t nnz, const uint32_t* __restrict__ dense, uint32_t* __restrict__ src,
-                         uint32_t* __restrict__ dst) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t e0 = t * kExpandChunk;
-    if (e0 >= nnz) return;
-    int64_t e1 = e0 + kExpandChunk < nnz ? e0 + kExpandChunk : nnz;
-    int64_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (off[mid] <= e0) lo = mid; else hi = mid;
-    }
-    int64_t r = lo, rend = off[r + 1];
-    uint32_t cr = dense[r];
-    for (int64_t e = e0; e < e1; ++e) {
-        while (e >= rend && r + 1 < n) {
-            ++r;
-            rend = off[r + 1];
-            cr = dense[r];
-        }
-        uint32_t j = (uint32_t)cols[e];
-        src[e] = cr;
+                         uint32_t* __restrict__ dst, Globals* glob) {
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t e0 = warp * kWalkTile;
+    if (e0 >= nnz) return;  // the whole warp
+    const int64_t e1 = e0 + kWalkTile < nnz ? e0 + kWalkTile : nnz;
+    const bool ok = warp_walk(off, n, e0, e1, [&](int64_t e, int64_t r) {
+        src[e] = dense[r];
+        const uint32_t j = (uint32_t)cols[e];
         dst[e] = j < (uint32_t)n ? dense[j] : 0u;
-    }
+    });
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(&glob->err, kErrBadOffsets);
 }
 
 // Stable LSD radix sort pass on 8-bit digits of key (shift), carrying two
@@ -414,10 +404,10 @@ cudaError_t launch_mg_compact(const AggScratch& a, const uint32_t* keep, const u
 }
 
 cudaError_t launch_expand(const int64_t* off, const int32_t* cols, int64_t n, int64_t nnz, const uint32_t* dense,
-                          uint32_t* src, uint32_t* dst, cudaStream_t s) {
+                          uint32_t* src, uint32_t* dst, Globals* glob, cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
-    int64_t threads = (nnz + kExpandChunk - 1) / kExpandChunk;
-    k_expand<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(off, cols, n, nnz, dense, src, dst);
+    const int64_t warps = (nnz + kWalkTile - 1) / kWalkTile;
+    k_expand<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, cols, n, nnz, dense, src, dst, glob);
     return cudaGetLastError();
 }
 

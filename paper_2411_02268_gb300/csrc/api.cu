@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "batch.cuh"
@@ -86,7 +87,7 @@ struct Scratch {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int check_csr(const cd_csr* g) {
+int check_csr(const cd_csr* g, bool scan_host = true) {
     if (!g) return CD_EINVAL;
     if (g->n < 0 || g->n >= 0x7FFFFFFFLL || g->nnz < 0) return CD_EINVAL;
     if (g->memory != CD_MEM_DEVICE && g->memory != CD_MEM_HOST) return CD_EINVAL;
@@ -99,11 +100,35 @@ int check_csr(const cd_csr* g) {
         // kernels that read them (device-side error flags)
         const int64_t* off = g->offsets;
         if (off[0] != 0 || off[g->n] != g->nnz) return CD_EINVAL;
-        for (int64_t i = 0; i < g->n; ++i)
-            if (off[i + 1] < off[i]) return CD_EINVAL;
+        if (scan_host)
+            for (int64_t i = 0; i < g->n; ++i)
+                if (off[i + 1] < off[i]) return CD_EINVAL;
     }
     return CD_OK;
 }
+
+// The O(n) checks of host inputs (offsets in order, labels below n), run on
+// a host thread while the call stages the inputs on the device.
+struct HostCheck {
+    std::thread t;
+    int rc = CD_OK;
+    void start(const cd_csr* g, const uint32_t* labels) {
+        if (g->memory != CD_MEM_HOST) return;
+        t = std::thread([this, g, labels]() {
+            const int64_t* off = g->offsets;
+            for (int64_t i = 0; i < g->n; ++i)
+                if (off[i + 1] < off[i]) { rc = CD_EINVAL; return; }
+            if (labels)
+                for (int64_t i = 0; i < g->n; ++i)
+                    if ((int64_t)labels[i] >= g->n) { rc = CD_EINVAL; return; }
+        });
+    }
+    int join() {
+        if (t.joinable()) t.join();
+        return rc;
+    }
+    ~HostCheck() { join(); }
+};
 
 void default_schedule(int k, cd_schedule* s) {
     // Streams per row by row length: one stream up to 128 entries, then about
@@ -195,6 +220,7 @@ struct Level {
     bool reuse = false;   // prepare_level keeps the buffers of an earlier call (schedule trials)
     uint32_t *tc = nullptr, *to = nullptr;  // bucketing scratch
     int64_t* dstarts = nullptr;
+    unsigned long long* btiles = nullptr;   // scan scratch of the bucketing
     BucketTable bt;     // bucket layout; ranges of colour class 0
     int colors = 1;
     std::vector<int64_t> starts;  // (colour, bucket) range starts, colors * nb + 1
@@ -240,7 +266,8 @@ int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cud
 // K, totals from `labels`, buckets by (colour class, row length); reads back
 // 2m, max K and the bucket ranges.
 int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, bool exact,
-                  const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s) {
+                  const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s,
+                  bool singletons = false) {
     const bool fresh = !L.reuse || !L.K;
     if (fresh) {
         CD_TRY(sc.get(&L.K, L.n));
@@ -257,12 +284,13 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
         CD_TRY(sc.get(&L.tc, ntiles * cap));
         CD_TRY(sc.get(&L.to, ntiles * cap));
         CD_TRY(sc.get(&L.dstarts, cap + 1));
+        CD_TRY(sc.get(&L.btiles, scan_tiles(ntiles * cap) + 1));
     }
     uint32_t *tc = L.tc, *to = L.to;
     int64_t* starts = L.dstarts;
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
     CD_CUDA(launch_bucket(L.off, L.n, L.nnz, L.bt, colors, L.cid, tc, to, starts, L.verts, labels, labels_out_copy,
-                          dglob, s));
+                          dglob, s, L.btiles));
     HostGlobals hg;
     CD_TRY(read_globals(dglob, starts, nkeys, &hg, s));
     L.starts.assign(hg.starts, hg.starts + nkeys + 1);
@@ -271,7 +299,7 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
     CD_CUDA(cudaMemsetAsync(L.K, 0, sizeof(uint64_t) * (size_t)(L.n > 0 ? L.n : 1), s));
     for (int c = 0; c < colors; ++c)
         CD_CUDA(launch_row_sums(L.off, L.w, L.n, L.nnz, L.verts, L.table_for(c), L.K, dglob, s));
-    CD_CUDA(launch_totals(labels, L.K, L.n, L.Sigma, L.size, dglob, s));
+    CD_CUDA(launch_totals(singletons ? nullptr : labels, L.K, L.n, L.Sigma, L.size, dglob, s));
     CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
     L.two_m = hg.g.two_m;
     if (L.two_m >= (1ull << 62)) return CD_EOVERFLOW;
@@ -393,7 +421,7 @@ int aggregate_level(const Level& L, const uint32_t* dense, int64_t nc, Scratch& 
     if (scan_tiles(nc + 1) > tiles) tiles = scan_tiles(nc + 1);
     CD_TRY(sc.get(&a.tiles, tiles + 1));
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
-    CD_CUDA(launch_expand(L.off, L.cols, L.n, m, dense, a.src, a.dst, s));
+    CD_CUDA(launch_expand(L.off, L.cols, L.n, m, dense, a.src, a.dst, dglob, s));
     if (m > 0) CD_CUDA(cudaMemcpyAsync(a.w, L.w, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s));
     CD_CUDA(radix_sort_pairs(a, m, nc, dglob, s));
     CD_CUDA(launch_heads(a, m, s));
@@ -667,7 +695,7 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     if (init) CD_CUDA(cudaMemcpyAsync(la, init, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
     else CD_CUDA(launch_iota(la, L.n, s));
     const int colors = resolve_colors(p);
-    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
+    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s, init == nullptr));
     const int rule = trace ? 0 : p->skip_rule;
     const bool track = rule != 0 || trace;
     uint8_t *active = nullptr, *moved_last = nullptr, *since_move = nullptr;
@@ -871,7 +899,7 @@ int refine_level(Level& L, const cd_params* p, const uint32_t* bound, const cd_s
     CD_TRY(sc.get(&L.movers, L.n));
     CD_CUDA(launch_iota(la, L.n, s));
     const int colors = resolve_colors(p);
-    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s));
+    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s, true));
     const size_t stat_off = offsetof(Globals, moved);
     const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
     CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
@@ -1048,7 +1076,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
              const uint8_t* active, const uint32_t* bound, uint32_t* labels_out, int64_t* moved_out,
              uint64_t* gain_out) {
     reset_stats();
-    CD_TRY(check_csr(g));
+    CD_TRY(check_csr(g, false));  // the O(n) host checks run beside the staging (HostCheck)
     CD_TRY(check_params(p));
     if (mode != CD_MODE_LOUVAIN && mode != CD_MODE_LPA && mode != CD_MODE_REFINE) return CD_EINVAL;
     if ((mode == CD_MODE_REFINE) != (bound != nullptr)) return CD_EINVAL;
@@ -1059,10 +1087,8 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     cd_schedule sched;
     if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     const bool host = g->memory == CD_MEM_HOST;
-    if (host) {
-        for (int64_t i = 0; i < g->n; ++i)
-            if ((int64_t)labels_in[i] >= g->n) return CD_EINVAL;
-    }
+    HostCheck hc;
+    hc.start(g, labels_in);
     Scratch sc(s);
     Level L;
     L.n = g->n;
@@ -1070,7 +1096,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     const uint32_t* lin = labels_in;
     uint32_t* lout = labels_out;
     const uint8_t* act = active;
-    if (host) {
+    auto stage = [&]() -> int {
         int64_t *off; int32_t* cols; uint32_t* w; uint32_t* li;
         CD_TRY(stage_in(g->offsets, g->n + 1, &off, sc));
         CD_TRY(stage_in(g->cols, g->nnz, &cols, sc));
@@ -1080,6 +1106,12 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         if (active) { uint8_t* da; CD_TRY(stage_in(active, g->n, &da, sc)); act = da; }
         if (bound) { uint32_t* db; CD_TRY(stage_in(bound, g->n, &db, sc)); bound = db; }
         L.off = off; L.cols = cols; L.w = w; lin = li;
+        return CD_OK;
+    };
+    if (host) {
+        const int st = stage();
+        CD_TRY(hc.join());  // bad host inputs are reported as such, staged or not
+        CD_TRY(st);
     } else {
         L.off = g->offsets; L.cols = g->cols; L.w = g->weights;
     }
@@ -1121,7 +1153,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
 int cd_modularity(const cd_csr* g, const uint32_t* labels, void* stream, double* q_out,
                   cd_modularity_parts* parts) {
     reset_stats();
-    CD_TRY(check_csr(g));
+    CD_TRY(check_csr(g, false));
     if (!labels) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
@@ -1130,14 +1162,20 @@ int cd_modularity(const cd_csr* g, const uint32_t* labels, void* stream, double*
     const uint32_t* w = g->weights;
     const uint32_t* lab = labels;
     if (g->memory == CD_MEM_HOST) {
-        for (int64_t i = 0; i < g->n; ++i)
-            if ((int64_t)labels[i] >= g->n) return CD_EINVAL;
-        int64_t* doff; int32_t* dc; uint32_t* dw; uint32_t* dl;
-        CD_TRY(stage_in(g->offsets, g->n + 1, &doff, sc));
-        CD_TRY(stage_in(g->cols, g->nnz, &dc, sc));
-        CD_TRY(stage_in(g->weights, g->nnz, &dw, sc));
-        CD_TRY(stage_in(labels, g->n, &dl, sc));
-        off = doff; cols = dc; w = dw; lab = dl;
+        HostCheck hc;
+        hc.start(g, labels);
+        auto stage = [&]() -> int {
+            int64_t* doff; int32_t* dc; uint32_t* dw; uint32_t* dl;
+            CD_TRY(stage_in(g->offsets, g->n + 1, &doff, sc));
+            CD_TRY(stage_in(g->cols, g->nnz, &dc, sc));
+            CD_TRY(stage_in(g->weights, g->nnz, &dw, sc));
+            CD_TRY(stage_in(labels, g->n, &dl, sc));
+            off = doff; cols = dc; w = dw; lab = dl;
+            return CD_OK;
+        };
+        const int st = stage();
+        CD_TRY(hc.join());
+        CD_TRY(st);
     }
     Globals* dglob;
     uint64_t *K, *Sig;
@@ -1471,7 +1509,7 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
         const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
         // median time of one full sweep of the batch with schedule sc_try and k
         auto time_sweep = [&](const cd_schedule& st, int k, double* ms_out) -> int {
-            CD_TRY(prepare_level(L, la, lb, k == 0, st, 1, sc, dglob, s));
+            CD_TRY(prepare_level(L, la, lb, k == 0, st, 1, sc, dglob, s, true));
             CD_CUDA(launch_graph_two_m(L.K, dvb, dnv, G, two_m_g, s));
             SweepArgs a = make_args(L, la, lb, nullptr, nullptr, dglob, CD_MODE_LOUVAIN, p->subtract);
             a.gid = gid0;

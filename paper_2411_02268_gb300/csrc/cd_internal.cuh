@@ -140,6 +140,7 @@ __device__ __forceinline__ bool barred(const SweepArgs& a, uint32_t c, uint32_t 
 // Host-side launchers (sweep.cu).
 cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,
                            uint64_t* K, Globals* glob, cudaStream_t s);
+// Sigma_c and |c| from labels (null: singletons), 2m and max K_i into glob.
 cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,
                           uint32_t* size, Globals* glob, cudaStream_t s);
 // Bucketing by (colour class, bucket): tile_counts / tile_offsets need
@@ -152,7 +153,7 @@ int64_t bucket_tiles(int64_t n);
 cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
                           const uint32_t* cid, uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
-                          Globals* glob, cudaStream_t s);
+                          Globals* glob, cudaStream_t s, unsigned long long* scan_scratch = nullptr);
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s);
 // Compaction of the bucketed vertex list to the vertices whose active byte is
 // set, order kept: cverts (n_listed), per colour class the new ranges in
@@ -209,7 +210,7 @@ struct AggScratch {
     unsigned long long *wsum, *tiles;
 };
 cudaError_t launch_expand(const int64_t* off, const int32_t* cols, int64_t n, int64_t nnz, const uint32_t* dense,
-                          uint32_t* src, uint32_t* dst, cudaStream_t s);
+                          uint32_t* src, uint32_t* dst, Globals* glob, cudaStream_t s);
 cudaError_t radix_sort_pairs(AggScratch& a, int64_t nnz, int64_t nc, Globals* glob, cudaStream_t s);
 cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_dst, Globals* glob, cudaStream_t s);
 int bits_for(int64_t nc);

@@ -3,43 +3,34 @@
 // sum_c sigma_c = sum of w over CSR entries (i, j) with C_i = C_j, and
 // Sigma_c = sum of K_i over the members of c.
 #include "cd_internal.cuh"
+#include "csr_walk.cuh"
 
 namespace cdk {
 
-constexpr int kQChunk = 64;
+constexpr int64_t kQTile = 4096;  // CSR entries per warp
 
-// sum_c sigma_c: each thread scans a 64-entry chunk of the CSR and walks the
-// rows it covers.
+// sum_c sigma_c: one warp per 4096-entry tile walks the entries with their
+// rows (csr_walk.cuh), coalesced.
 __global__ void k_sigma_in(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
                            const uint32_t* __restrict__ w, const uint32_t* __restrict__ labels, int64_t n,
                            int64_t nnz, Globals* glob) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t e0 = t * kQChunk;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t e0 = warp * kQTile;
+    if (e0 >= nnz) return;  // the whole warp
+    const int64_t e1 = e0 + kQTile < nnz ? e0 + kQTile : nnz;
     unsigned long long sum = 0;
-    if (e0 < nnz) {
-        int64_t e1 = e0 + kQChunk < nnz ? e0 + kQChunk : nnz;
-        int64_t lo = 0, hi = n;
-        while (hi - lo > 1) {
-            int64_t mid = (lo + hi) >> 1;
-            if (off[mid] <= e0) lo = mid; else hi = mid;
-        }
-        int64_t r = lo, rend = off[r + 1];
-        uint32_t cr = labels[r];
-        for (int64_t e = e0; e < e1; ++e) {
-            while (e >= rend && r + 1 < n) {
-                ++r;
-                rend = off[r + 1];
-                cr = labels[r];
-            }
-            if (e >= rend) { atomicOr(&glob->err, kErrBadOffsets); break; }
-            uint32_t j = (uint32_t)cols[e];
-            if (j >= (uint32_t)n) { atomicOr(&glob->err, kErrBadCol); continue; }
-            if (__ldg(labels + j) == cr) sum += w[e];
-        }
-    }
+    bool badcol = false;
+    const bool ok = warp_walk(off, n, e0, e1, [&](int64_t e, int64_t r) {
+        const uint32_t j = (uint32_t)cols[e];
+        if (j >= (uint32_t)n) { badcol = true; return; }
+        if (__ldg(labels + j) == labels[r]) sum += w[e];
+    });
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&glob->sigma_in, sum);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0 && sum) atomicAdd(&glob->sigma_in, sum);
+    if (lane == 0 && !ok) atomicOr(&glob->err, kErrBadOffsets);
+    if (badcol) atomicOr(&glob->err, kErrBadCol);
 }
 
 // sum_c Sigma_c^2 as a 128-bit integer (two 64-bit halves with carry).
@@ -76,8 +67,8 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* cols, const uin
     cudaError_t e = launch_totals(labels, K, n, Sigma_scratch, sizes_scratch, glob, s);
     if (e != cudaSuccess) return e;
     if (nnz > 0) {
-        int64_t threads = (nnz + kQChunk - 1) / kQChunk;
-        k_sigma_in<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(off, cols, w, labels, n, nnz, glob);
+        const int64_t warps = (nnz + kQTile - 1) / kQTile;
+        k_sigma_in<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, cols, w, labels, n, nnz, glob);
     }
     k_sum_sq<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const unsigned long long*)Sigma_scratch, n, glob);
     return cudaGetLastError();

@@ -4,6 +4,7 @@
 #include <cstdio>
 
 #include "cd_internal.cuh"
+#include "csr_walk.cuh"
 
 namespace cdk {
 
@@ -12,48 +13,57 @@ namespace cdk {
 // the weight array and adds per-row partial sums with atomics, so hub rows
 // are split across threads and every thread does the same work.
 // ---------------------------------------------------------------------------
-constexpr int kDegChunk = 64;
+constexpr int64_t kDegTile = 4096;  // CSR entries per warp
 
+// K_i = sum of w over row i: one warp per 4096-entry tile walks the entries
+// with their rows (csr_walk.cuh); each step's lanes of one row are summed by a
+// segmented shuffle reduction and the row's first lane adds the sum to K.
 __global__ void k_degrees(const int64_t* __restrict__ off, const uint32_t* __restrict__ w,
                           int64_t n, int64_t nnz, unsigned long long* __restrict__ K, Globals* glob) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t e0 = t * kDegChunk;
-    if (e0 >= nnz) return;
-    int64_t e1 = e0 + kDegChunk < nnz ? e0 + kDegChunk : nnz;
-    int64_t lo = 0, hi = n;  // off[lo] <= e0 < off[hi] (or hi == n)
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (off[mid] <= e0) lo = mid; else hi = mid;
-    }
-    int64_t r = lo, rend = off[r + 1];
-    unsigned long long sum = 0;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t e0 = warp * kDegTile;
+    if (e0 >= nnz) return;  // the whole warp
+    const int64_t e1 = e0 + kDegTile < nnz ? e0 + kDegTile : nnz;
+    const int lane = threadIdx.x & 31;
     bool zero = false;
-    for (int64_t e = e0; e < e1; ++e) {
-        while (e >= rend && r + 1 < n) {
-            if (sum) atomicAdd(&K[r], sum);
-            sum = 0;
-            ++r;
-            rend = off[r + 1];
+    const bool ok = warp_walk<true>(off, n, e0, e1, [&](int64_t e, int64_t r, bool valid) {
+        unsigned long long v = 0;
+        if (valid) {
+            const uint32_t x = __ldg(w + e);
+            zero |= x == 0;
+            v = x;
         }
-        if (e >= rend) {  // offsets do not cover the entries
-            atomicOr(&glob->err, kErrBadOffsets);
-            return;
+        const int64_t row = valid ? r : -1;
+        // lanes of one row are consecutive: sum each lane's run to the right
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v2 = __shfl_down_sync(0xffffffffu, v, o);
+            const int64_t r2 = __shfl_down_sync(0xffffffffu, row, o);
+            if (lane + o < 32 && r2 == row) v += v2;
         }
-        uint32_t x = __ldg(w + e);
-        zero |= x == 0;
-        sum += x;
-    }
-    if (sum) atomicAdd(&K[r], sum);
+        const int64_t prev = __shfl_up_sync(0xffffffffu, row, 1);
+        if (valid && (lane == 0 || prev != row) && v) atomicAdd(&K[row], v);
+    });
+    if (lane == 0 && !ok) atomicOr(&glob->err, kErrBadOffsets);
     if (zero) atomicOr(&glob->err, kErrZeroWeight);
+}
+
+// Offsets in order, starting at 0 and ending at nnz (kErrBadOffsets).
+__global__ void k_check_offsets(const int64_t* __restrict__ off, int64_t n, int64_t nnz, Globals* glob) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t a = off[i], b = off[i + 1];
+    if (b < a || (i == 0 && a != 0) || (i == n - 1 && b != nnz)) atomicOr(&glob->err, kErrBadOffsets);
 }
 
 cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,
                            uint64_t* K, Globals* glob, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(K, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
-    if (e != cudaSuccess || nnz == 0) return e;
-    int64_t threads = (nnz + kDegChunk - 1) / kDegChunk;
-    int64_t blocks = (threads + 255) / 256;
-    k_degrees<<<(unsigned)blocks, 256, 0, s>>>(off, w, n, nnz, (unsigned long long*)K, glob);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_check_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, n, nnz, glob);
+    if (nnz == 0) return cudaGetLastError();
+    const int64_t warps = (nnz + kDegTile - 1) / kDegTile;
+    k_degrees<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, w, n, nnz, (unsigned long long*)K, glob);
     return cudaGetLastError();
 }
 
@@ -65,12 +75,18 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
     unsigned long long k = 0;
     if (i < n) {
         k = K[i];
-        uint32_t c = labels[i];
-        if ((int64_t)c < n) {
-            if (k) atomicAdd(&Sigma[c], k);
-            atomicAdd(&size[c], 1u);
+        if (!labels) {
+            // singleton communities (labels = vertex ids): plain stores
+            Sigma[i] = k;
+            size[i] = 1u;
         } else {
-            atomicOr(&glob->err, kErrBadLabel);
+            uint32_t c = labels[i];
+            if ((int64_t)c < n) {
+                if (k) atomicAdd(&Sigma[c], k);
+                atomicAdd(&size[c], 1u);
+            } else {
+                atomicOr(&glob->err, kErrBadLabel);
+            }
         }
     }
     // block reduction, then one atomic per block (a single address would
@@ -199,8 +215,11 @@ cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, in
 
 cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, uint64_t* Sigma,
                           uint32_t* size, Globals* glob, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(Sigma, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), s);
+    cudaError_t e = cudaSuccess;
+    if (labels) {  // null labels: singletons, every entry is stored
+        e = cudaMemsetAsync(Sigma, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), s);
+    }
     if (e != cudaSuccess || n == 0) return e;
     k_totals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(labels, (const unsigned long long*)K, n,
                                                           (unsigned long long*)Sigma, size, glob);
@@ -334,13 +353,20 @@ __global__ void k_bucket_starts(const uint32_t* __restrict__ tile_offsets, int64
 cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const BucketTable& bt, int colors,
                           const uint32_t* cid, uint32_t* tile_counts, uint32_t* tile_offsets, int64_t* bucket_starts,
                           uint32_t* verts, const uint32_t* labels_in, uint32_t* labels_out,
-                          Globals* glob, cudaStream_t s) {
+                          Globals* glob, cudaStream_t s, unsigned long long* scan_scratch) {
     const int nkeys = colors * bt.nb;
     if (nkeys > kMaxKeys) return cudaErrorInvalidValue;
     if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (nkeys + 1), s);
     int64_t ntiles = bucket_tiles(n);
     k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_counts, ntiles, glob);
-    k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, ntiles * nkeys, &glob->count);
+    const int64_t m = ntiles * nkeys;
+    if (scan_scratch && m > 65536) {
+        // large tables: the tiled scan (one block would take hundreds of us)
+        cudaError_t e = launch_exclusive_scan_u32(tile_counts, tile_offsets, m, scan_scratch, &glob->count, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, m, &glob->count);
+    }
     k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_offsets, ntiles, verts,
                                                       labels_in, labels_out);
     k_bucket_starts<<<1, 256, 0, s>>>(tile_offsets, ntiles, nkeys, &glob->count, bucket_starts);
@@ -377,6 +403,9 @@ cudaError_t launch_agg_mg(const AggArgs& g, int k, bool wide, int64_t nblocks, c
 
 cudaError_t launch_sweep_mg(const SweepArgs& a, int k, bool wide, int64_t nblocks, cudaStream_t s) {
     if (nblocks == 0) return cudaSuccess;
+    // a compacted list needs at most its full-list block count, and a few
+    // resident waves stride over it
+    if (a.dr && nblocks > 152 * 8) nblocks = 152 * 8;
     if (k >= 32)  // these sketch sizes merge inside one warp
         for (int b = 0; b < a.bt.nb; ++b)
             if (a.bt.lanes[b] > 32) return cudaErrorInvalidValue;

@@ -722,62 +722,63 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(
     __shared__ SweepSmem<K, VT> sm;
     extern __shared__ __align__(16) unsigned char dyn_smem[];  // k >= 32: one WarpStage per warp
     __shared__ EpiSmem esm;
-    // blocks of the longest rows first, so that they start at once and
-    // overlap with the many short rows instead of trailing the launch
-    int64_t blk;
-    int b = 0;
-    int64_t vb0, vb1, bb0;
-    if (a.dr) {
-        // compacted list: the grid covers the full list, blocks past the
-        // compacted one leave at once (the whole block: no barrier is reached)
-        const int64_t total = a.dr->bbegin[a.bt.nb];
-        if ((int64_t)blockIdx.x >= total) return;
-        blk = total - 1 - (int64_t)blockIdx.x;
+    // Virtual blocks, the longest rows first, so that they start at once and
+    // overlap with the many short rows instead of trailing the launch.  A
+    // full sweep runs one virtual block per grid block; a skip sweep over the
+    // compacted list (ranges on the device) runs a smaller grid that strides
+    // over its virtual blocks.
+    const int64_t nvirt = a.dr ? a.dr->bbegin[a.bt.nb] : (int64_t)gridDim.x;
+    for (int64_t j = blockIdx.x; j < nvirt; j += gridDim.x) {
+        if (j != (int64_t)blockIdx.x) __syncthreads();  // the previous virtual block is done with shared memory
+        const int64_t blk = nvirt - 1 - j;
+        int b = 0;
+        int64_t vb0, vb1, bb0;
+        if (a.dr) {
 #pragma unroll
-        for (int q = 1; q < CD_MAX_BUCKETS; ++q)
-            if (q < a.bt.nb && blk >= a.dr->bbegin[q]) b = q;
-        bb0 = a.dr->bbegin[b];
-        vb0 = a.dr->vbegin[b];
-        vb1 = a.dr->vbegin[b + 1];
-    } else {
-        blk = (int64_t)gridDim.x - 1 - (int64_t)blockIdx.x;
+            for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+                if (q < a.bt.nb && blk >= a.dr->bbegin[q]) b = q;
+            bb0 = a.dr->bbegin[b];
+            vb0 = a.dr->vbegin[b];
+            vb1 = a.dr->vbegin[b + 1];
+        } else {
 #pragma unroll
-        for (int q = 1; q < CD_MAX_BUCKETS; ++q)
-            if (q < a.bt.nb && blk >= a.bt.bbegin[q]) b = q;
-        bb0 = a.bt.bbegin[b];
-        vb0 = a.bt.vbegin[b];
-        vb1 = a.bt.vbegin[b + 1];
-    }
-    const int L = a.bt.lanes[b];
-    const int64_t lb = blk - bb0;
-    const int vpb = L >= kBlock ? 1 : kBlock / L;
-    const int64_t vi = vb0 + lb * vpb + threadIdx.x / L;
-    const bool valid = vi < vb1;
-    Outcome o;
-    if constexpr (K >= 32) {
-        WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
-        switch (L) {  // the host caps L at 32 for these sketch sizes
-            case 1: o = group_body_big<1, K, VT>(a, vi, valid, ws); break;
-            case 2: o = group_body_big<2, K, VT>(a, vi, valid, ws); break;
-            case 4: o = group_body_big<4, K, VT>(a, vi, valid, ws); break;
-            case 8: o = group_body_big<8, K, VT>(a, vi, valid, ws); break;
-            case 16: o = group_body_big<16, K, VT>(a, vi, valid, ws); break;
-            default: o = group_body_big<32, K, VT>(a, vi, valid, ws); break;
+            for (int q = 1; q < CD_MAX_BUCKETS; ++q)
+                if (q < a.bt.nb && blk >= a.bt.bbegin[q]) b = q;
+            bb0 = a.bt.bbegin[b];
+            vb0 = a.bt.vbegin[b];
+            vb1 = a.bt.vbegin[b + 1];
         }
-    } else {
-        switch (L) {
-            case 1: o = group_body<1, K, VT>(a, vi, valid); break;
-            case 2: o = group_body<2, K, VT>(a, vi, valid); break;
-            case 4: o = group_body<4, K, VT>(a, vi, valid); break;
-            case 8: o = group_body<8, K, VT>(a, vi, valid); break;
-            case 16: o = group_body<16, K, VT>(a, vi, valid); break;
-            case 32: o = group_body<32, K, VT>(a, vi, valid); break;
-            case 64: o = block_body<64, K, VT>(a, vi, valid, sm); break;
-            case 128: o = block_body<128, K, VT>(a, vi, valid, sm); break;
-            default: o = block_body<256, K, VT>(a, vi, valid, sm); break;
+        const int L = a.bt.lanes[b];
+        const int64_t lb = blk - bb0;
+        const int vpb = L >= kBlock ? 1 : kBlock / L;
+        const int64_t vi = vb0 + lb * vpb + threadIdx.x / L;
+        const bool valid = vi < vb1;
+        Outcome o;
+        if constexpr (K >= 32) {
+            WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
+            switch (L) {  // the host caps L at 32 for these sketch sizes
+                case 1: o = group_body_big<1, K, VT>(a, vi, valid, ws); break;
+                case 2: o = group_body_big<2, K, VT>(a, vi, valid, ws); break;
+                case 4: o = group_body_big<4, K, VT>(a, vi, valid, ws); break;
+                case 8: o = group_body_big<8, K, VT>(a, vi, valid, ws); break;
+                case 16: o = group_body_big<16, K, VT>(a, vi, valid, ws); break;
+                default: o = group_body_big<32, K, VT>(a, vi, valid, ws); break;
+            }
+        } else {
+            switch (L) {
+                case 1: o = group_body<1, K, VT>(a, vi, valid); break;
+                case 2: o = group_body<2, K, VT>(a, vi, valid); break;
+                case 4: o = group_body<4, K, VT>(a, vi, valid); break;
+                case 8: o = group_body<8, K, VT>(a, vi, valid); break;
+                case 16: o = group_body<16, K, VT>(a, vi, valid); break;
+                case 32: o = group_body<32, K, VT>(a, vi, valid); break;
+                case 64: o = block_body<64, K, VT>(a, vi, valid, sm); break;
+                case 128: o = block_body<128, K, VT>(a, vi, valid, sm); break;
+                default: o = block_body<256, K, VT>(a, vi, valid, sm); break;
+            }
         }
+        block_epilogue(a, o, esm);
     }
-    block_epilogue(a, o, esm);
 }
 
 // ---------------------------------------------------------------------------

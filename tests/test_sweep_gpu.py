@@ -370,3 +370,21 @@ def test_large_sketch_rejects_wide_streams(env):
     s = sched_for(cd, 64, *WIDE)
     with pytest.raises(cd.CDError):
         gpu_sweep(cd, torch, g, np.arange(g.n, dtype=np.uint32), oracle.MODE_LOUVAIN, 64, sched=s)
+
+
+def test_modularity_rejects_offsets_short_of_the_entries(env):
+    """Device offsets that end before the last entry are reported (the warp
+    walk over the entries stops instead of reading past the offsets)."""
+    cd, torch = env
+    g = GRAPHS["rmat12_w16"]()
+    off = g.offsets.copy()
+    off[-1] -= 5  # the last row ends 5 entries early
+    bad = cd.Graph(g.n, torch.from_numpy(off).cuda(), torch.from_numpy(g.cols).cuda(),
+                   torch.from_numpy(g.w.view(np.int32)).cuda())
+    lab = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(cd.CDError) as e:
+        cd.cd_modularity(bad, lab)
+    assert e.value.code == cd.CD_EINVAL
+    # and the well-formed graph still gives the oracle's parts afterwards
+    q, parts = cd.cd_modularity(cd.Graph.to_device(g), lab)
+    assert parts == oracle.modularity_parts(g, np.arange(g.n, dtype=np.uint32))
