@@ -267,7 +267,7 @@ int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cud
 // 2m, max K and the bucket ranges.
 int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, bool exact,
                   const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s,
-                  bool singletons = false) {
+                  bool singletons = false, cudaEvent_t weights_ready = nullptr) {
     const bool fresh = !L.reuse || !L.K;
     if (fresh) {
         CD_TRY(sc.get(&L.K, L.n));
@@ -297,6 +297,7 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
     // weighted degrees row by row over the buckets (one launch per colour
     // class), then community totals
     CD_CUDA(cudaMemsetAsync(L.K, 0, sizeof(uint64_t) * (size_t)(L.n > 0 ? L.n : 1), s));
+    if (weights_ready) CD_CUDA(cudaStreamWaitEvent(s, weights_ready, 0));
     for (int c = 0; c < colors; ++c)
         CD_CUDA(launch_row_sums(L.off, L.w, L.n, L.nnz, L.verts, L.table_for(c), L.K, dglob, s));
     CD_CUDA(launch_totals(singletons ? nullptr : labels, L.K, L.n, L.Sigma, L.size, dglob, s));
@@ -367,6 +368,28 @@ int stage_in(const T* host, int64_t count, T** dev, Scratch& sc) {
     if (count > 0) CD_CUDA(cudaMemcpyAsync(*dev, host, sizeof(T) * count, cudaMemcpyHostToDevice, sc.s));
     return CD_OK;
 }
+
+// Host inputs copied on a side stream in the order the call needs them
+// (offsets and labels, then weights, then columns), with an event after each
+// group, so that degree bucketing and row sums run while the columns still
+// copy.
+struct SideCopies {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    int init() {
+        CD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        for (auto& e : ev) CD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return CD_OK;
+    }
+    ~SideCopies() {
+        // the copies finish before the scratch they fill is released (a call
+        // that fails part-way has not made its stream wait for them)
+        if (cs) cudaStreamSynchronize(cs);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
 
 struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -1096,15 +1119,38 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     const uint32_t* lin = labels_in;
     uint32_t* lout = labels_out;
     const uint8_t* act = active;
+    SideCopies side;
     auto stage = [&]() -> int {
+        // allocations are ordered on s; the copies run on the side stream
         int64_t *off; int32_t* cols; uint32_t* w; uint32_t* li;
-        CD_TRY(stage_in(g->offsets, g->n + 1, &off, sc));
-        CD_TRY(stage_in(g->cols, g->nnz, &cols, sc));
-        CD_TRY(stage_in(g->weights, g->nnz, &w, sc));
-        CD_TRY(stage_in(labels_in, g->n, &li, sc));
+        CD_TRY(side.init());
+        CD_TRY(sc.get(&off, g->n + 1));
+        CD_TRY(sc.get(&li, g->n));
+        CD_TRY(sc.get(&w, g->nnz));
+        CD_TRY(sc.get(&cols, g->nnz));
         CD_TRY(sc.get(&lout, g->n));
-        if (active) { uint8_t* da; CD_TRY(stage_in(active, g->n, &da, sc)); act = da; }
-        if (bound) { uint32_t* db; CD_TRY(stage_in(bound, g->n, &db, sc)); bound = db; }
+        uint8_t* da = nullptr;
+        uint32_t* db = nullptr;
+        if (active) CD_TRY(sc.get(&da, g->n));
+        if (bound) CD_TRY(sc.get(&db, g->n));
+        CD_CUDA(cudaEventRecord(side.ev[0], s));
+        CD_CUDA(cudaStreamWaitEvent(side.cs, side.ev[0], 0));  // the allocations precede the copies
+        CD_CUDA(cudaMemcpyAsync(off, g->offsets, sizeof(int64_t) * (g->n + 1), cudaMemcpyHostToDevice, side.cs));
+        if (g->n > 0) {
+            CD_CUDA(cudaMemcpyAsync(li, labels_in, sizeof(uint32_t) * g->n, cudaMemcpyHostToDevice, side.cs));
+            if (da) CD_CUDA(cudaMemcpyAsync(da, active, g->n, cudaMemcpyHostToDevice, side.cs));
+            if (db) CD_CUDA(cudaMemcpyAsync(db, bound, sizeof(uint32_t) * g->n, cudaMemcpyHostToDevice, side.cs));
+        }
+        if (da) act = da;
+        if (db) bound = db;
+        CD_CUDA(cudaEventRecord(side.ev[0], side.cs));
+        if (g->nnz > 0) CD_CUDA(cudaMemcpyAsync(w, g->weights, sizeof(uint32_t) * g->nnz, cudaMemcpyHostToDevice,
+                                                side.cs));
+        CD_CUDA(cudaEventRecord(side.ev[1], side.cs));
+        if (g->nnz > 0) CD_CUDA(cudaMemcpyAsync(cols, g->cols, sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
+                                                side.cs));
+        CD_CUDA(cudaEventRecord(side.ev[2], side.cs));
+        CD_CUDA(cudaStreamWaitEvent(s, side.ev[0], 0));  // offsets and labels before the bucketing
         L.off = off; L.cols = cols; L.w = w; lin = li;
         return CD_OK;
     };
@@ -1122,7 +1168,8 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         if (gain_out) { gain_out[0] = 0; gain_out[1] = 0; }
         return CD_OK;
     }
-    CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, 1, sc, dglob, s));
+    CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, 1, sc, dglob, s, false, host ? side.ev[1] : nullptr));
+    if (host) CD_CUDA(cudaStreamWaitEvent(s, side.ev[2], 0));  // the columns before the sweep
     SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, resolve_colors(p), p->sub_color);
     a.one_scan = p->one_scan;
     Timer tm;
