@@ -300,7 +300,10 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
     if (weights_ready) CD_CUDA(cudaStreamWaitEvent(s, weights_ready, 0));
     for (int c = 0; c < colors; ++c)
         CD_CUDA(launch_row_sums(L.off, L.w, L.n, L.nnz, L.verts, L.table_for(c), L.K, dglob, s));
-    CD_CUDA(launch_totals(singletons ? nullptr : labels, L.K, L.n, L.Sigma, L.size, dglob, s));
+    // singletons: known to the caller, or found by the bucketing (no label
+    // differs from its vertex id: glob->pad stayed 0)
+    const bool single = singletons || (labels && hg.g.pad == 0);
+    CD_CUDA(launch_totals(single ? nullptr : labels, L.K, L.n, L.Sigma, L.size, dglob, s));
     CD_TRY(read_globals(dglob, nullptr, 0, &hg, s));
     L.two_m = hg.g.two_m;
     if (L.two_m >= (1ull << 62)) return CD_EOVERFLOW;

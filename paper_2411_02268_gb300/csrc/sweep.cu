@@ -9,9 +9,8 @@
 namespace cdk {
 
 // ---------------------------------------------------------------------------
-// K_i = sum of w over row i (Section 3).  Each thread sums a 64-entry chunk of
-// the weight array and adds per-row partial sums with atomics, so hub rows
-// are split across threads and every thread does the same work.
+// K_i = sum of w over row i (Section 3), over the whole CSR (the modularity
+// path; the sweeps sum the rows by bucket, k_row_sums below).
 // ---------------------------------------------------------------------------
 constexpr int64_t kDegTile = 4096;  // CSR entries per warp
 
@@ -259,22 +258,26 @@ __device__ __forceinline__ int key_of(const int64_t* __restrict__ off, int64_t v
 
 int64_t bucket_tiles(int64_t n) { return (n + kBucketTile - 1) / kBucketTile; }
 
+// Also sets glob->pad when some label differs from its vertex id (labels
+// not null), so that the caller can take the singleton path of the totals.
 __global__ void k_bucket_count(const int64_t* __restrict__ off, int64_t n, int64_t nnz, BucketTable bt, int colors,
-                               const uint32_t* __restrict__ cid, uint32_t* __restrict__ tile_counts, int64_t ntiles,
-                               Globals* glob) {
+                               const uint32_t* __restrict__ cid, const uint32_t* __restrict__ labels,
+                               uint32_t* __restrict__ tile_counts, int64_t ntiles, Globals* glob) {
     __shared__ uint32_t cnt[kMaxKeys];
     const int nkeys = colors * bt.nb;
     cnt[threadIdx.x] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * kBucketTile;
+    bool other = false;
     for (int r = 0; r < kBucketTile / 256; ++r) {
         int64_t v = base + r * 256 + threadIdx.x;
         if (v < n) {
             int key = key_of(off, v, n, nnz, bt, colors, cid, glob);
             if (key >= 0) atomicAdd(&cnt[key], 1u);
+            if (labels && labels[v] != (uint32_t)v) other = true;
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(other) && threadIdx.x == 0) atomicOr(&glob->pad, 1u);
     if ((int)threadIdx.x < nkeys) tile_counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
@@ -358,7 +361,8 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
     if (nkeys > kMaxKeys) return cudaErrorInvalidValue;
     if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (nkeys + 1), s);
     int64_t ntiles = bucket_tiles(n);
-    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_counts, ntiles, glob);
+    k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, labels_in, tile_counts, ntiles,
+                                                     glob);
     const int64_t m = ntiles * nkeys;
     if (scan_scratch && m > 65536) {
         // large tables: the tiled scan (one block would take hundreds of us)

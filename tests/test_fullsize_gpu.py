@@ -64,3 +64,16 @@ def test_rmat22_exact_variant_sampled_parity(env):
     cd, torch = env
     g = gen.rmat22(1)
     sampled_parity(cd, torch, g, np.arange(g.n, dtype=np.uint32), 0, oracle.MODE_LOUVAIN, nsample=2000)
+
+
+@pytest.mark.slow
+def test_rmat25_full_size_sampled_parity(env):
+    """The HBM-scale graph (R-MAT scale 25, edge factor 16, w in [1, 255]:
+    about 1.07 G CSR entries, hubs of ~10^6 entries on 256 streams): sampled
+    vertices and the largest hubs against the oracle, Louvain and LPA."""
+    cd, torch = env
+    g = gen.rmat25(1)
+    assert g.n == 2**25 and g.nnz > 900_000_000
+    single = np.arange(g.n, dtype=np.uint32)
+    sampled_parity(cd, torch, g, single, 8, oracle.MODE_LOUVAIN, nsample=3000, seed=3)
+    sampled_parity(cd, torch, g, single, 8, oracle.MODE_LPA, nsample=2000, seed=4)
