@@ -255,9 +255,10 @@ def learned_vs_plain(cd, torch, side: int, rmat_scale: int = 0):
 def variants_vs_exact(cd, torch, G):
     """The paper's comparison (Section 5.2-5.4): each method with its MG
     sketch size against the exact hashtable (k = 0) and weighted Boyer-Moore
-    (k = 1): modularity, wall time of the whole detection (device-resident
-    graph) and peak device scratch; on the bench graph, and Louvain k = 8
-    against exact on the 10k planted-partition graph (100 blocks, p_in 0.05,
+    (k = 1), and the weighted Misra-Gries of the literature (subtract = 2)
+    beside the paper's rule: modularity, wall time of the whole detection
+    (device-resident graph) and peak device scratch; on the bench graph, and
+    Louvain k = 8 against exact on the 10k planted-partition graph (100 blocks, p_in 0.05,
     p_out 0.0005) and on a rewired 1024 x 1024 grid."""
     from paper_2411_02268_gb300 import gen
 
@@ -276,20 +277,22 @@ def variants_vs_exact(cd, torch, G):
         out[a]["q_vs_exact"] = out[a]["q"] / out[b]["q"] if out[b]["q"] else None
         out[a]["time_vs_exact"] = out[a]["ms"] / out[b]["ms"]
 
-    runs = [("louvain", 8, {}), ("louvain", 1, {}), ("louvain", 0, {}),
+    runs = [("louvain", 8, {}), ("louvain", 8, {"subtract": 2}), ("louvain", 1, {}), ("louvain", 0, {}),
             ("leiden", 64, {}), ("leiden", 8, {}), ("leiden", 0, {}),
             ("lpa", 8, {}), ("lpa", 8, {"one_scan": True}), ("lpa", 0, {})]
     out = {}
     for method, k, kw in runs:
-        name = f"{method}_k{k}" + ("_1scan" if kw.get("one_scan") else "")
+        name = f"{method}_k{k}" + ("_1scan" if kw.get("one_scan") else "") + ("_textbook" if kw.get("subtract") else "")
         out[name] = one(G, method, k, kw)
-    for method, k in (("louvain", 8), ("louvain", 1), ("leiden", 64), ("leiden", 8), ("lpa", 8)):
-        vs(out, f"{method}_k{k}", f"{method}_k0")
+    for name in ("louvain_k8", "louvain_k8_textbook", "louvain_k1", "leiden_k64", "leiden_k8", "lpa_k8"):
+        vs(out, name, name.split("_")[0] + "_k0")
     for gname, make in (("sbm10k", lambda: gen.sbm_10k(1)), ("grid1024", lambda: gen.grid(1024, 1024, 0.02, 16, 1))):
         Gx = cd.Graph.to_device(make())
         r = {f"louvain_k{k}": one(Gx, "louvain", k, {}) for k in (8, 0)}
+        r["louvain_k8_textbook"] = one(Gx, "louvain", 8, {"subtract": 2})
         r.update({f"leiden_k{k}": one(Gx, "leiden", k, {}) for k in (64, 0)})
         vs(r, "louvain_k8", "louvain_k0")
+        vs(r, "louvain_k8_textbook", "louvain_k0")
         vs(r, "leiden_k64", "leiden_k0")
         out[gname] = r
     return out

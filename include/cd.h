@@ -108,7 +108,11 @@ typedef struct cd_params {
     int32_t k;            /* MG slots: 1, 2, 4, 8, 16, 32 or 64; 0 = exact hashtable.  With
                              32 or 64 slots (the paper's Leiden uses 64, Section 5.3) a
                              schedule may give a row at most 32 streams */
-    int32_t subtract;     /* 0 = conditional (Algorithm 1), 1 = unconditional (Section 4.1) */
+    int32_t subtract;     /* 0 = conditional (Algorithm 1), 1 = unconditional (Section 4.1),
+                             2 = the weighted Misra-Gries summary of the literature (no free
+                             slot: every slot loses min(w, smallest value) and the rest of w
+                             is inserted; not the paper's rule, offered for comparison; k <= 8
+                             and agg_k = 0 only) */
     double tolerance;     /* Louvain: stop a pass when the sweep's summed delta-Q <= tolerance;
                              LPA: stop when at most tolerance * n labels changed (Section 3.5) */
     double tolerance_drop;/* Louvain: tolerance divided by this after each pass (>= 1) */

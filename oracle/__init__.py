@@ -148,18 +148,18 @@ def new_sketch(k: int):
     return np.full(k, EMPTY_KEY, dtype=np.uint32), np.zeros(k, dtype=np.uint64)
 
 
-def sketch_update(keys, vals, c: int, w: int, uncond: bool = False):
+def sketch_update(keys, vals, c: int, w: int, uncond: int = 0):
     """One populateSketch update (in place) with community c and weight w."""
     assert keys.dtype == np.uint32 and vals.dtype == np.uint64 and keys.flags.c_contiguous
     _load().or_sketch_update(_ptr(keys), _ptr(vals), len(keys), c, w, int(uncond))
 
 
-def sketch_merge(akeys, avals, bkeys, bvals, uncond: bool = False):
+def sketch_merge(akeys, avals, bkeys, bvals, uncond: int = 0):
     _load().or_sketch_merge(_ptr(akeys), _ptr(avals), _ptr(bkeys), _ptr(bvals), len(akeys),
                             int(uncond))
 
 
-def sketch_stream(stream, k: int, uncond: bool = False):
+def sketch_stream(stream, k: int, uncond: int = 0):
     """Sketch of a (community, weight) stream processed in order."""
     keys, vals = new_sketch(k)
     for c, w in stream:
@@ -197,7 +197,7 @@ def row_sketch(g, i: int, labels, k: int, sched: Schedule, uncond=False, bound=N
 
 # ---- one synchronous sweep ----------------------------------------------------------
 
-def sweep(g, labels, mode: int = MODE_LOUVAIN, k: int = 8, uncond: bool = False,
+def sweep(g, labels, mode: int = MODE_LOUVAIN, k: int = 8, uncond: int = 0,
           sched: Schedule | None = None, active=None, bound=None, vertices=None,
           threads: int = 1, state=None, colors: int = 1, sub_color: int = 0, one_scan: bool = False):
     """One synchronous sweep from `labels` (see or_sweep in oracle.c).
@@ -292,7 +292,7 @@ def aggregate(g, labels):
     return G2, dense
 
 
-def aggregate_mg(g, labels, k: int = 8, uncond: bool = False, sched: Schedule | None = None,
+def aggregate_mg(g, labels, k: int = 8, uncond: int = 0, sched: Schedule | None = None,
                  symmetric: bool = False):
     """MG aggregation (Section 4.1, Fig. 3): super-vertex c links to the live
     slots of one MG sketch over all edges of c's members (no second pass).

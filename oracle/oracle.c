@@ -84,9 +84,10 @@ void or_modularity_parts(int64_t n, const int64_t* off, const int32_t* cols, con
  *   2. if some slot's key is c (live or zeroed), stop;
  *   3. else put (c, w) into the empty slot with the largest index;
  *   4. else subtract w from every slot, clamping at 0 (the new key is dropped).
- * Unconditional variant (Section 4.1, "unconditional subtraction"): when c
+ * Unconditional variant (Section 4.1, unconditional subtraction): when c
  * is not present, subtract w (clamped) from every slot first, then insert
- * into the largest-index empty slot if one exists.
+ * into the largest-index empty slot if one exists.  uncond = 2 selects the
+ * weighted Misra-Gries summary of the literature instead (below).
  * ------------------------------------------------------------------------- */
 void or_sketch_update(uint32_t* keys, uint64_t* vals, int k, uint32_t c, uint64_t w, int uncond) {
     int has = 0;
@@ -94,6 +95,28 @@ void or_sketch_update(uint32_t* keys, uint64_t* vals, int k, uint32_t c, uint64_
         if (keys[p] == c) { vals[p] += w; has = 1; }
     }
     if (has) return;
+    if (uncond == 2) {
+        /* the weighted Misra-Gries summary of the literature (not the paper's
+         * rule): a free slot takes (c, w); otherwise every slot loses
+         * d = min(w, smallest value) and what is left of w, if anything, goes
+         * into the largest-index slot that fell to 0 */
+        int e = -1;
+        for (int p = 0; p < k; ++p)
+            if (vals[p] == 0) e = p;
+        if (e >= 0) { keys[e] = c; vals[e] = w; return; }
+        uint64_t m = vals[0];
+        for (int p = 1; p < k; ++p)
+            if (vals[p] < m) m = vals[p];
+        const uint64_t d = w < m ? w : m;
+        for (int p = 0; p < k; ++p) vals[p] -= d;
+        if (w > d) {
+            for (int p = 0; p < k; ++p)
+                if (vals[p] == 0) e = p;
+            keys[e] = c;
+            vals[e] = w - d;
+        }
+        return;
+    }
     if (uncond) {
         for (int p = 0; p < k; ++p) vals[p] = vals[p] > w ? vals[p] - w : 0;
     }

@@ -163,7 +163,9 @@ int check_params(const cd_params* p) {
     if (!(p->k == 0 || p->k == 1 || p->k == 2 || p->k == 4 || p->k == 8 || p->k == 16 || p->k == 32 ||
           p->k == 64))
         return CD_EINVAL;
-    if (p->subtract != 0 && p->subtract != 1) return CD_EINVAL;
+    if (p->subtract < 0 || p->subtract > 2) return CD_EINVAL;
+    // the textbook summary is compiled for sketches of up to 8 slots, sweeps only
+    if (p->subtract == 2 && (p->k > 8 || p->agg_k != 0)) return CD_EINVAL;
     if (p->one_scan != 0 && p->one_scan != 1) return CD_EINVAL;
     if (p->one_scan && p->k == 0) return CD_EINVAL;
     if (!(p->agg_k == 0 || p->agg_k == 1 || p->agg_k == 2 || p->agg_k == 4 || p->agg_k == 8 || p->agg_k == 16))

@@ -21,6 +21,16 @@ namespace cdk {
 // running subtraction total turned a subtraction into one add but made every
 // accumulation dearer; on R-MAT 22 it was 15% slower overall.)
 // ---------------------------------------------------------------------------
+// Tag selecting the weighted Misra-Gries of the literature (subtract = 2).
+struct TextbookMG {};
+
+template <typename U>
+__device__ __forceinline__ U mode_of(const SweepArgs& a);
+template <>
+__device__ __forceinline__ int mode_of<int>(const SweepArgs& a) { return a.uncond; }
+template <>
+__device__ __forceinline__ TextbookMG mode_of<TextbookMG>(const SweepArgs&) { return TextbookMG{}; }
+
 template <int K, typename VT>
 struct Sketch {
     uint32_t key[K];
@@ -36,11 +46,12 @@ struct Sketch {
     __device__ __forceinline__ VT value(int p) const { return t[p]; }
 
     // Algorithm 1 for one (c, w): add w to the slot holding c (a slot whose
-    // value fell to 0 keeps its key and revives); otherwise (unconditional:
-    // after subtracting w from every slot) put c into the largest-index empty
-    // slot (value 0), found by a downward search; with no empty slot
-    // (conditional) subtract w from every slot, clamping at 0.
-    __device__ __forceinline__ void update(uint32_t c, VT w, bool uncond) {
+    // value fell to 0 keeps its key and revives); otherwise (unconditional,
+    // mode 1: after subtracting w from every slot) put c into the
+    // largest-index empty slot (value 0), found by a downward search; with no
+    // empty slot (conditional, mode 0) subtract w from every slot, clamping
+    // at 0.
+    __device__ __forceinline__ void update(uint32_t c, VT w, int mode) {
         bool has = false;
 #pragma unroll
         for (int p = 0; p < K; ++p) {
@@ -49,25 +60,55 @@ struct Sketch {
             has |= m;
         }
         if (!has) {
-            if (uncond) {
+            if (mode) {
 #pragma unroll
                 for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
                 lossy = true;
             }
-            bool done = false;
-#pragma unroll
-            for (int p = K - 1; p >= 0; --p) {
-                const bool z = !done && t[p] == 0;
-                key[p] = z ? c : key[p];
-                t[p] = z ? w : t[p];
-                done |= z;
-            }
-            if (!done && !uncond) {
+            bool done = insert_top(c, w);
+            if (!done && !mode) {
 #pragma unroll
                 for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
                 lossy = true;
             }
         }
+    }
+
+    // The weighted Misra-Gries summary of the literature (subtract = 2, not
+    // the paper's rule): with no empty slot every slot loses d = min(w,
+    // smallest value) and the rest of w, if any, goes into the largest-index
+    // slot that fell to 0.  A separate overload (selected at compile time), so
+    // that the paper's modes keep their code.
+    __device__ __forceinline__ void update(uint32_t c, VT w, TextbookMG) {
+        bool has = false;
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            const bool m = key[p] == c;
+            t[p] += m ? w : (VT)0;
+            has |= m;
+        }
+        if (!has && !insert_top(c, w)) {
+            VT d = w;
+#pragma unroll
+            for (int p = 0; p < K; ++p) d = t[p] < d ? t[p] : d;
+#pragma unroll
+            for (int p = 0; p < K; ++p) t[p] -= d;
+            lossy = true;
+            if (d < w) insert_top(c, w - d);
+        }
+    }
+
+    // (c, w) into the largest-index empty slot, if any.
+    __device__ __forceinline__ bool insert_top(uint32_t c, VT w) {
+        bool done = false;
+#pragma unroll
+        for (int p = K - 1; p >= 0; --p) {
+            const bool z = !done && t[p] == 0;
+            key[p] = z ? c : key[p];
+            t[p] = z ? w : t[p];
+            done |= z;
+        }
+        return done;
     }
 };
 
@@ -244,9 +285,9 @@ struct Outcome {
 };
 
 // Feeds the live slots of a partner sketch (keys pk, values pv) to s.
-template <int K, typename VT>
+template <int K, typename VT, typename U>
 __device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk)[K], const VT (&pv)[K],
-                                           bool plossy, bool unc) {
+                                           bool plossy, U unc) {
 #pragma unroll
     for (int p = 0; p < K; ++p)
         if (pv[p] > 0) s.update(pk[p], pv[p], unc);
@@ -255,8 +296,8 @@ __device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk
 
 // Merge tree over the G streams of a group inside one warp: S[s] <- merge(S[s],
 // S[s+o]) for o = G/2 .. 1; lane 0 ends with the row's sketch.
-template <int G, int K, typename VT>
-__device__ __forceinline__ void group_merge(Sketch<K, VT>& sk, int lane, unsigned gmask, bool unc) {
+template <int G, int K, typename VT, typename U>
+__device__ __forceinline__ void group_merge(Sketch<K, VT>& sk, int lane, unsigned gmask, U unc) {
 #pragma unroll 1
     for (int o = G / 2; o >= 1; o >>= 1) {
         uint32_t pk[K];
@@ -303,7 +344,7 @@ __device__ __forceinline__ int tab_find(const uint32_t* tk, uint32_t c) {
 // ---------------------------------------------------------------------------
 // G streams per vertex inside one warp (G = 1, 2, ..., 32).
 // ---------------------------------------------------------------------------
-template <int G, int K, typename VT>
+template <int G, int K, typename VT, typename U>
 __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bool valid, PassTwoTabs<VT>* tabs) {
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu
@@ -327,7 +368,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     }
     Sketch<K, VT> sk;
     sk.init();
-    const bool unc = a.uncond != 0;
+    const U unc = mode_of<U>(a);
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
     if (act) {
@@ -455,7 +496,7 @@ struct WarpStage {
     };
 };
 
-template <int G, int K, typename VT>
+template <int G, int K, typename VT, typename U>
 __device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi, bool valid,
                                                   WarpStage<K, VT>& ws) {
     const int lane = threadIdx.x & (G - 1);
@@ -480,7 +521,7 @@ __device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi
     }
     Sketch<K, VT> sk;
     sk.init();
-    const bool unc = a.uncond != 0;
+    const U unc = mode_of<U>(a);
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
     if (act) scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
@@ -579,9 +620,9 @@ __device__ __forceinline__ void sub_barrier(int id, int nthreads) {
 // Merge tree over the L = 64..256 streams of a sub-block: cross-warp rounds
 // (o = L/2 .. 32) through shared memory, then in-warp rounds (o = 16 .. 1) in
 // the sub-block's first warp; thread s = 0 ends with the row's sketch.
-template <int L, int K, typename VT>
+template <int L, int K, typename VT, typename U>
 __device__ __forceinline__ void block_merge(Sketch<K, VT>& sk, int s, int sb, int bar, BlockSmem<K, VT>& sm,
-                                            bool unc) {
+                                            U unc) {
     const int slot_base = sb * (L / 2);  // (256/L) sub-blocks x L/2 slots = 128
 #pragma unroll 1
     for (int o = L / 2; o >= 32; o >>= 1) {
@@ -606,10 +647,10 @@ __device__ __forceinline__ void block_merge(Sketch<K, VT>& sk, int s, int sb, in
         }
         sub_barrier(bar, L);
     }
-    if ((s >> 5) == 0) group_merge<32, K, VT>(sk, s & 31, 0xffffffffu, unc);
+    if ((s >> 5) == 0) group_merge<32, K, VT, U>(sk, s & 31, 0xffffffffu, unc);
 }
 
-template <int L, int K, typename VT>
+template <int L, int K, typename VT, typename U>
 __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bool valid,
                                               BlockSmem<K, VT>& sm) {
     constexpr int W = L / 32;
@@ -637,13 +678,13 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     }
     Sketch<K, VT> sk;
     sk.init();
-    const bool unc = a.uncond != 0;
+    const U unc = mode_of<U>(a);
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((s - (int)(c0 & (L - 1))) & (L - 1));
     if (act) {
         scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
     }
-    block_merge<L, K, VT>(sk, s, sb, bar, sm, unc);
+    block_merge<L, K, VT, U>(sk, s, sb, bar, sm, unc);
     if (wl == 0 && lane == 0) {
 #pragma unroll
         for (int p = 0; p < K; ++p) {
@@ -792,7 +833,7 @@ constexpr int sweep_min_blocks() {
     return K >= 32 ? 1 : ((K >= 16 || sizeof(VT) == 8) ? 2 : 4);
 }
 
-template <int K, typename VT>
+template <int K, typename VT, typename U>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(const SweepArgs a) {
     __shared__ SweepSmem<K, VT> sm;
     extern __shared__ __align__(16) unsigned char dyn_smem[];  // k >= 32: one WarpStage per warp
@@ -832,24 +873,24 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(
         if constexpr (K >= 32) {
             WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
             switch (L) {  // the host caps L at 32 for these sketch sizes
-                case 1: o = group_body_big<1, K, VT>(a, vi, valid, ws); break;
-                case 2: o = group_body_big<2, K, VT>(a, vi, valid, ws); break;
-                case 4: o = group_body_big<4, K, VT>(a, vi, valid, ws); break;
-                case 8: o = group_body_big<8, K, VT>(a, vi, valid, ws); break;
-                case 16: o = group_body_big<16, K, VT>(a, vi, valid, ws); break;
-                default: o = group_body_big<32, K, VT>(a, vi, valid, ws); break;
+                case 1: o = group_body_big<1, K, VT, U>(a, vi, valid, ws); break;
+                case 2: o = group_body_big<2, K, VT, U>(a, vi, valid, ws); break;
+                case 4: o = group_body_big<4, K, VT, U>(a, vi, valid, ws); break;
+                case 8: o = group_body_big<8, K, VT, U>(a, vi, valid, ws); break;
+                case 16: o = group_body_big<16, K, VT, U>(a, vi, valid, ws); break;
+                default: o = group_body_big<32, K, VT, U>(a, vi, valid, ws); break;
             }
         } else {
             switch (L) {
-                case 1: o = group_body<1, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 2: o = group_body<2, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 4: o = group_body<4, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 8: o = group_body<8, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 16: o = group_body<16, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 32: o = group_body<32, K, VT>(a, vi, valid, tabs_of(sm)); break;
-                case 64: o = block_body<64, K, VT>(a, vi, valid, sm.b); break;
-                case 128: o = block_body<128, K, VT>(a, vi, valid, sm.b); break;
-                default: o = block_body<256, K, VT>(a, vi, valid, sm.b); break;
+                case 1: o = group_body<1, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 2: o = group_body<2, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 4: o = group_body<4, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 8: o = group_body<8, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 16: o = group_body<16, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 32: o = group_body<32, K, VT, U>(a, vi, valid, tabs_of(sm)); break;
+                case 64: o = block_body<64, K, VT, U>(a, vi, valid, sm.b); break;
+                case 128: o = block_body<128, K, VT, U>(a, vi, valid, sm.b); break;
+                default: o = block_body<256, K, VT, U>(a, vi, valid, sm.b); break;
             }
         }
         block_epilogue(a, o, esm);
@@ -894,7 +935,7 @@ __device__ __forceinline__ void agg_group(const AggArgs& g, int64_t vi, bool val
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu
                                      : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    const bool unc = g.a.uncond != 0;
+    const int unc = g.a.uncond;
     Sketch<K, VT> sk;
     sk.init();
     uint32_t c = 0;
@@ -910,7 +951,7 @@ template <int L, int K, typename VT>
 __device__ __forceinline__ void agg_block(const AggArgs& g, int64_t vi, bool valid, BlockSmem<K, VT>& sm) {
     const int sb = threadIdx.x / L;
     const int s = threadIdx.x % L;
-    const bool unc = g.a.uncond != 0;
+    const int unc = g.a.uncond;
     Sketch<K, VT> sk;
     sk.init();
     uint32_t c = 0;
@@ -918,7 +959,7 @@ __device__ __forceinline__ void agg_block(const AggArgs& g, int64_t vi, bool val
         c = g.a.verts[vi];
         for_members<K, VT>(g, c, s, L, [&](uint32_t key, uint32_t w) { sk.update(key, (VT)w, unc); });
     }
-    block_merge<L, K, VT>(sk, s, sb, 1 + sb, sm, unc);
+    block_merge<L, K, VT, int>(sk, s, sb, 1 + sb, sm, unc);
     if (valid && s == 0) agg_store(g, c, sk);
 }
 
@@ -956,16 +997,27 @@ cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStrea
     return cudaGetLastError();
 }
 
-template <int K, typename VT>
-cudaError_t launch_k_vt(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
+template <int K, typename VT, typename U>
+cudaError_t launch_k_mode(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
     size_t dyn = 0;
     if constexpr (K >= 32) {
         dyn = sizeof(WarpStage<K, VT>) * (kBlock / 32);
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_mg<K, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_sweep_mg<K, VT, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
-    k_sweep_mg<K, VT><<<(unsigned)nblocks, kBlock, dyn, s>>>(a);
+    k_sweep_mg<K, VT, U><<<(unsigned)nblocks, kBlock, dyn, s>>>(a);
     return cudaGetLastError();
+}
+
+// subtract = 2 (the textbook summary) is compiled for k <= 8 only
+template <int K, typename VT>
+cudaError_t launch_k_vt(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
+    if (a.uncond == 2) {
+        if constexpr (K <= 8) return launch_k_mode<K, VT, TextbookMG>(a, nblocks, s);
+        else return cudaErrorInvalidValue;
+    }
+    return launch_k_mode<K, VT, int>(a, nblocks, s);
 }
 
 template <int K>

@@ -97,7 +97,7 @@ def test_argument_checks_without_gpu(cd):
     assert rc(cd.make_params(k=3)) == cd.CD_EINVAL
     assert rc(cd.make_params(k=128)) == cd.CD_EINVAL
     assert rc(cd.make_params(k=64, schedule=cd.schedule_from([10**9], [64]))) == cd.CD_EINVAL  # > 32 streams
-    assert rc(cd.make_params(k=8, subtract=2)) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=8, subtract=3)) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8), mode=7) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8), lo=lab) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8, one_scan=True), mode=cd.MODE_LOUVAIN) == cd.CD_EINVAL

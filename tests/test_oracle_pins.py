@@ -84,6 +84,43 @@ def test_sketch_exact_when_few_communities(seed):
     assert got == exact
 
 
+@pytest.mark.parametrize("seed", range(20))
+def test_textbook_weighted_mg_bound(seed):
+    """subtract = 2 is the weighted Misra-Gries summary of the literature:
+    every decrement removes (k + 1) d of weight (d from each slot and d of the
+    incoming item), so each estimate lies in [f - W/(k+1), f] for weighted
+    streams of total W, and every key heavier than W/(k+1) survives.  The
+    paper's clamped rule has no such guarantee (vector V3)."""
+    rng = np.random.default_rng(300 + seed)
+    k = int(rng.choice([1, 2, 4, 8]))
+    ncomm = int(rng.integers(2, 40))
+    p = rng.pareto(1.0, ncomm) + 1e-3
+    p /= p.sum()
+    n = int(rng.integers(1, 300))
+    stream = [(int(c), int(rng.integers(1, 17))) for c in rng.choice(ncomm, size=n, p=p)]
+    W = sum(w for _, w in stream)
+    keys, vals = oracle.sketch_stream(stream, k, uncond=2)
+    f = np.zeros(ncomm, dtype=np.int64)
+    for c, w in stream:
+        f[c] += w
+    est = {int(kk): int(v) for kk, v in zip(keys, vals) if v > 0}
+    for c in range(ncomm):
+        e = est.get(c, 0)
+        assert e <= f[c]
+        assert e >= f[c] - W / (k + 1) - 1e-9
+        if f[c] > W / (k + 1):
+            assert c in est
+
+
+def test_textbook_weighted_mg_keeps_v3_majority():
+    """Vector V3 under the textbook rule: (b,1) then (a,3) with k = 1 keeps a
+    with 3 - 1 = 2 (the paper's clamped rule loses a)."""
+    keys, vals = oracle.sketch_stream([(11, 1), (10, 3)], 1, uncond=2)
+    assert keys.tolist() == [10] and vals.tolist() == [2]
+    keys, vals = oracle.sketch_stream([(11, 1), (10, 3)], 1)
+    assert vals.tolist() == [0]
+
+
 def test_sketch_weighted_bm_k1_majority():
     """k=1 weighted Boyer-Moore keeps a key whose weight exceeds the rest of
     the stream when it comes first in a run (sanity of the k=1 case)."""

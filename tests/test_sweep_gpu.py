@@ -57,7 +57,7 @@ def gpu_sweep(cd, torch, g, labels, mode, k, uncond=0, sched=None, active=None, 
 
 def oracle_sweep(cd, g, labels, mode, k, uncond=0, sched=None, active=None):
     sch = oracle_sched(cd, sched if sched is not None else cd.cd_default_schedule(k))
-    out, gains = oracle.sweep(g, labels, mode, k, bool(uncond), sch, active=active, threads=4)
+    out, gains = oracle.sweep(g, labels, mode, k, int(uncond), sch, active=active, threads=4)
     moved = int(np.count_nonzero(out != np.asarray(labels, dtype=np.uint32)))
     return out, moved, oracle.gain_total(gains)
 
@@ -122,6 +122,9 @@ def test_mg_lpa_and_unconditional(env, gname, k):
         check(cd, torch, g, lab, oracle.MODE_LPA, k)
         check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, uncond=1)
         check(cd, torch, g, lab, oracle.MODE_LPA, k, uncond=1, sched=s)
+        # the weighted Misra-Gries of the literature (subtract = 2)
+        check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, uncond=2)
+        check(cd, torch, g, lab, oracle.MODE_LPA, k, uncond=2, sched=s)
 
 
 @pytest.mark.parametrize("gname", list(GRAPHS))
@@ -362,6 +365,17 @@ def test_large_sketch_wide_values(env, k):
     for _, lab in label_states(g, 8):
         check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k)
         check(cd, torch, g, lab, oracle.MODE_LPA, k)
+
+
+def test_textbook_summary_limits(env):
+    """subtract = 2 is compiled for k <= 8 sweeps only: larger k and MG
+    aggregation are refused."""
+    cd, torch = env
+    g = GRAPHS["sbm10k"]()
+    for kw in (dict(k=16, subtract=2), dict(k=64, subtract=2), dict(k=8, subtract=2, agg_k=4)):
+        with pytest.raises(cd.CDError) as e:
+            cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(**kw))
+        assert e.value.code == cd.CD_EINVAL
 
 
 def test_large_sketch_rejects_wide_streams(env):
