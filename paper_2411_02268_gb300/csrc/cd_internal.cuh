@@ -136,6 +136,12 @@ __device__ __forceinline__ bool barred(const SweepArgs& a, uint32_t c, uint32_t 
     if (a.mode == CD_MODE_REFINE) return a.size[c] == 1 && (int)color_of(c, a.colors) == a.sub_color;
     return d_single && c > d && a.size[c] == 1;
 }
+// barred() with |c| already loaded.
+__device__ __forceinline__ bool barred_n(const SweepArgs& a, uint32_t c, uint32_t d, bool d_single,
+                                         uint32_t size_c) {
+    if (a.mode == CD_MODE_REFINE) return size_c == 1 && (int)color_of(c, a.colors) == a.sub_color;
+    return d_single && c > d && size_c == 1;
+}
 
 // Host-side launchers (sweep.cu).
 cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz,

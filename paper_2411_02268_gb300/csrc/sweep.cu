@@ -116,8 +116,8 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
 // K_i = sum of w over row i for the rows listed in the bucket table.  Rows of
 // a bucket with L <= 32 streams are summed by L threads of a warp (one thread
 // per row for the short rows), rows of the wider buckets by a whole block;
-// 16-byte loads, four of them in flight per thread (the long rows are
-// otherwise latency-bound), then a shuffle (and shared-memory) reduction.
+// 16-byte loads, four of them in flight per thread (the rows are otherwise
+// latency-bound), then a shuffle (and shared-memory) reduction.
 // Each row's sum is written once; rows of length 0 are not listed and keep
 // K = 0.
 __device__ __forceinline__ uint4 load_w4(const uint32_t* __restrict__ w, int64_t ch, int64_t nnz) {
@@ -164,18 +164,18 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
         i = verts[vi];
         const int64_t start = off[i], end = off[i + 1];
         const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
-        int64_t ch = c0 + lane;
-        for (; ch + 3 * (int64_t)L < c1; ch += 4 * (int64_t)L) {
-            const uint4 v0 = load_w4(w, ch, nnz);
-            const uint4 v1 = load_w4(w, ch + L, nnz);
-            const uint4 v2 = load_w4(w, ch + 2 * L, nnz);
-            const uint4 v3 = load_w4(w, ch + 3 * L, nnz);
-            add_w4(v0, ch, start, end, sum, zero);
-            add_w4(v1, ch + L, start, end, sum, zero);
-            add_w4(v2, ch + 2 * L, start, end, sum, zero);
-            add_w4(v3, ch + 3 * L, start, end, sum, zero);
+        // four loads in flight per trip, each guarded (a lane's last trip is
+        // usually partial)
+        for (int64_t ch = c0 + lane; ch < c1; ch += 4 * (int64_t)L) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t cu = ch + u * (int64_t)L;
+                v[u] = cu < c1 ? load_w4(w, cu, nnz) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add_w4(v[u], ch + u * (int64_t)L, start, end, sum, zero);
         }
-        for (; ch < c1; ch += L) add_w4(load_w4(w, ch, nnz), ch, start, end, sum, zero);
     }
     if (L > 1) {
         const int G = L < 32 ? L : 32;
@@ -196,7 +196,9 @@ __global__ void __launch_bounds__(256) k_row_sums(const int64_t* __restrict__ of
 
 cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, int64_t nnz, const uint32_t* verts,
                             const BucketTable& bt_in, uint64_t* K, Globals* glob, cudaStream_t s) {
-    // geometry: L <= 32 threads per row, or a block per row for wider buckets
+    // geometry: the sweep's L <= 32 threads per row, or a block per row for
+    // wider buckets (more threads per row for the short-row buckets measured
+    // slower: 1.573 against 1.517 ms per R-MAT 22 sweep step)
     BucketTable bt = bt_in;
     int64_t blk = 0;
     for (int b = 0; b < bt.nb; ++b) {
@@ -364,8 +366,8 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
     k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, labels_in, tile_counts, ntiles,
                                                      glob);
     const int64_t m = ntiles * nkeys;
-    if (scan_scratch && m > 65536) {
-        // large tables: the tiled scan (one block would take hundreds of us)
+    if (scan_scratch && m > 4096) {
+        // larger tables: the tiled scan (one block took 24 us at 28K entries)
         cudaError_t e = launch_exclusive_scan_u32(tile_counts, tile_offsets, m, scan_scratch, &glob->count, s);
         if (e != cudaSuccess) return e;
     } else {

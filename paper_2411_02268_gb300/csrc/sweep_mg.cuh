@@ -133,18 +133,39 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
         best_w = bk;
     } else {
         const unsigned long long two_m = two_m_of(a, i);
-        const unsigned long long Ki = a.K[i];
-        const unsigned long long Sd = a.Sigma[d];
-        const bool sd1 = a.size[d] == 1;
+        const unsigned long long Ki = __ldg(a.K + i);
+        const unsigned long long Sd = __ldg(a.Sigma + d);
+        const bool sd1 = __ldg(a.size + d) == 1;
+        // the candidates' totals and sizes are requested four at a time before
+        // any is used, so that those gathers are in flight together (Sigma and
+        // size are read-only during a sweep; eight at a time spilled registers)
+        constexpr int kB = K < 4 ? K : 4;
         i128 bg = 0;
 #pragma unroll
-        for (int p = 0; p < K; ++p) {
-            uint32_t c = cand[p];
-            if (c == kEmpty) continue;
-            if (barred(a, c, d, sd1)) continue;
-            i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
-                     (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
-            if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; best_w = acc[p]; }
+        for (int b = 0; b < K; b += kB) {
+            unsigned long long sig[kB];
+            uint32_t siz[kB];
+#pragma unroll
+            for (int q = 0; q < kB; ++q) {
+                const uint32_t c = cand[b + q];
+                const bool ok = c != kEmpty;
+                sig[q] = ok ? __ldg(a.Sigma + c) : 0ull;
+                siz[q] = ok ? __ldg(a.size + c) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kB; ++q) {
+                const uint32_t c = cand[b + q];
+                if (c == kEmpty) continue;
+                if (barred_n(a, c, d, sd1, siz[q])) continue;
+                const i128 g = (i128)two_m * ((i128)acc[b + q] - (i128)kid) -
+                               (i128)Ki * ((i128)Ki + (i128)sig[q] - (i128)Sd);
+                if (g > 0 && (g > bg || (g == bg && c < best))) {
+                    best = c;
+                    bg = g;
+                    have = true;
+                    best_w = acc[b + q];
+                }
+            }
         }
         gain_out = have ? (u128)bg : (u128)0;
     }
