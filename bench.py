@@ -484,7 +484,7 @@ def main():
     while time.perf_counter() - t_w < args.warm_seconds:
         step()
     torch.cuda.synchronize()
-    kern_ms, kern_launches = 0.0, 0
+    kern_ms, kern_launches, all_launches = 0.0, 0, 0
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
@@ -498,6 +498,7 @@ def main():
             st = cd.cd_last_stats()
             kern_ms += st.sweep_kernel_ms
             kern_launches += st.sweep_kernel_launches
+            all_launches += st.kernel_launches  # every kernel of the library the step launched
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -564,7 +565,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "learned_vs_plain": learned,
             "batched_vs_plain": batched,
             "variants_vs_exact": variants,
-            "gpu_launches": 7 * args.steps, "clocks": clk.summary(),
+            "gpu_launches": all_launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
     if dist:

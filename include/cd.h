@@ -164,6 +164,8 @@ typedef struct cd_stats {
     int64_t entries_scanned; /* CSR entries of the vertices that decided (MG sweeps, all sweeps) */
     int64_t full_sweeps;     /* sweeps in which every vertex decided */
     char cuda_error[128];
+    int64_t kernel_launches; /* kernels of this library launched by the last call (a CUDA-graph
+                                replay counts the kernels recorded in the graph) */
 } cd_stats;
 
 /* Modularity parts (Eq. 1): Q = (two_m * sigma_in - sum_Sigma2) / two_m^2

@@ -42,9 +42,11 @@ cudaError_t launch_renumber(const uint32_t* labels, int64_t n, uint32_t* dense, 
     cudaError_t e = cudaMemsetAsync(scratch_n, 0, sizeof(uint32_t) * n, s);
     if (e != cudaSuccess) return e;
     unsigned nb = (unsigned)((n + 255) / 256);
+    note_launch();
     k_mark_used<<<nb, 256, 0, s>>>(labels, n, scratch_n, glob);
     e = launch_exclusive_scan_u32(scratch_n, scratch_n, n, tile_scratch, count_dev, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_apply_ids<<<nb, 256, 0, s>>>(labels, n, scratch_n, dense);
     return cudaGetLastError();
 }
@@ -57,6 +59,7 @@ __global__ void k_compose(uint32_t* __restrict__ top, int64_t n0, const uint32_t
 
 cudaError_t launch_compose(uint32_t* top, int64_t n0, const uint32_t* dense, cudaStream_t s) {
     if (n0 == 0) return cudaSuccess;
+    note_launch();
     k_compose<<<(unsigned)((n0 + 255) / 256), 256, 0, s>>>(top, n0, dense);
     return cudaGetLastError();
 }
@@ -68,6 +71,7 @@ __global__ void k_iota(uint32_t* __restrict__ x, int64_t n) {
 
 cudaError_t launch_iota(uint32_t* x, int64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n);
     return cudaGetLastError();
 }
@@ -83,6 +87,7 @@ __global__ void k_scatter_bound(const uint32_t* __restrict__ sub, const uint32_t
 cudaError_t launch_scatter_bound(const uint32_t* sub, const uint32_t* bound, int64_t n, uint32_t* next_init,
                                  cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_scatter_bound<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sub, bound, n, next_init);
     return cudaGetLastError();
 }
@@ -220,9 +225,11 @@ cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_d
             uint32_t* p1 = which == 0 ? a.src : a.dst;
             uint32_t* key_o = which == 0 ? a.dst2 : a.src2;
             uint32_t* p1_o = which == 0 ? a.src2 : a.dst2;
+            note_launch();
             k_radix_hist<<<(unsigned)nt, kRadixThreads, 0, s>>>(key, nnz, shift, a.hist, nt);
             cudaError_t e = launch_exclusive_scan_u32(a.hist, a.hist, hn, a.tiles, &glob->count, s);
             if (e != cudaSuccess) return e;
+            note_launch();
             k_radix_scatter<<<(unsigned)nt, kRadixThreads, 0, s>>>(key, p1, a.w, nnz, shift, a.hist, nt, key_o,
                                                                     p1_o, a.w2);
             std::swap(a.src, a.src2);
@@ -254,6 +261,7 @@ __global__ void k_community_counts(const int64_t* __restrict__ off, const uint32
 cudaError_t launch_community_counts(const int64_t* off, const uint32_t* dense, int64_t n, uint32_t* cnt,
                                     uint32_t* ecnt, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_community_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, dense, n, cnt, ecnt);
     return cudaGetLastError();
 }
@@ -368,6 +376,7 @@ __global__ void k_mg_compact(const uint32_t* __restrict__ src, const uint32_t* _
 cudaError_t launch_mg_sort_rows(uint32_t* keys, unsigned long long* vals, int64_t nc, int k, uint32_t* count,
                                 uint32_t* self_less, cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
+    note_launch();
     k_mg_sort_rows<<<(unsigned)((nc + 127) / 128), 128, 0, s>>>(keys, vals, nc, k, count, self_less);
     return cudaGetLastError();
 }
@@ -376,6 +385,7 @@ cudaError_t launch_mg_write_rows(const uint32_t* keys, const unsigned long long*
                                  const int64_t* roff, int32_t* cols_out, uint32_t* w_out, Globals* glob,
                                  cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
+    note_launch();
     k_mg_write_rows<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(keys, vals, nc, k, roff, cols_out, w_out, glob);
     return cudaGetLastError();
 }
@@ -384,6 +394,7 @@ cudaError_t launch_mg_candidates(const uint32_t* keys, const unsigned long long*
                                  const int64_t* fpos, const int64_t* rpos, int64_t R0, AggScratch& a, Globals* glob,
                                  cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
+    note_launch();
     k_mg_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(keys, vals, nc, k, fpos, rpos, R0, a.src, a.dst,
                                                                   a.w, glob);
     return cudaGetLastError();
@@ -391,6 +402,7 @@ cudaError_t launch_mg_candidates(const uint32_t* keys, const unsigned long long*
 
 cudaError_t launch_mg_select(const AggScratch& a, int64_t m, uint32_t* keep, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_mg_select<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a.src, a.dst, m, keep);
     return cudaGetLastError();
 }
@@ -398,6 +410,7 @@ cudaError_t launch_mg_select(const AggScratch& a, int64_t m, uint32_t* keep, cud
 cudaError_t launch_mg_compact(const AggScratch& a, const uint32_t* keep, const uint32_t* pos, int64_t m,
                               int32_t* cols_out, uint32_t* w_out, uint32_t* rowcnt, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_mg_compact<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(a.src, a.dst, a.w, keep, pos, m, cols_out, w_out,
                                                               rowcnt);
     return cudaGetLastError();
@@ -407,12 +420,14 @@ cudaError_t launch_expand(const int64_t* off, const int32_t* cols, int64_t n, in
                           uint32_t* src, uint32_t* dst, Globals* glob, cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     const int64_t warps = (nnz + kWalkTile - 1) / kWalkTile;
+    note_launch();
     k_expand<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, cols, n, nnz, dense, src, dst, glob);
     return cudaGetLastError();
 }
 
 cudaError_t launch_heads(const AggScratch& a, int64_t nnz, cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
+    note_launch();
     k_heads<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(a.src, a.dst, nnz, a.heads);
     return cudaGetLastError();
 }
@@ -420,6 +435,7 @@ cudaError_t launch_heads(const AggScratch& a, int64_t nnz, cudaStream_t s) {
 cudaError_t launch_segsum(const AggScratch& a, const uint32_t* uidx, int64_t nnz, int32_t* cols_out,
                           uint32_t* rowcnt, cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
+    note_launch();
     k_segsum<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(a.src, a.dst, a.w, a.heads, uidx, nnz, cols_out,
                                                             a.wsum, rowcnt);
     return cudaGetLastError();
@@ -428,6 +444,7 @@ cudaError_t launch_segsum(const AggScratch& a, const uint32_t* uidx, int64_t nnz
 cudaError_t launch_narrow(const unsigned long long* wsum, int64_t m, uint32_t* w_out, Globals* glob,
                           cudaStream_t s) {
     if (m == 0) return cudaSuccess;
+    note_launch();
     k_narrow<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(wsum, m, w_out, glob);
     return cudaGetLastError();
 }

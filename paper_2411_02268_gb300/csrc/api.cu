@@ -15,12 +15,17 @@
 
 using namespace cdk;
 
+namespace cdk {
+thread_local int64_t g_kernel_launches = 0;
+}  // namespace cdk
+
 namespace {
 
 thread_local cd_stats g_stats;
 
 void reset_stats() {
     std::memset(&g_stats, 0, sizeof(g_stats));
+    g_kernel_launches = 0;
 }
 
 int cuda_fail(cudaError_t e) {
@@ -683,6 +688,7 @@ struct Replay {
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;  // kernel launches recorded in the graph
     ~Replay() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -847,7 +853,11 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         for (int m = 0; m < (rule != 0 ? 2 : 1); ++m) {
             CD_CUDA(cudaStreamCreateWithFlags(&rp[m].cs, cudaStreamNonBlocking));
             CD_CUDA(cudaStreamBeginCapture(rp[m].cs, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = g_kernel_launches;
             const int rc = sweep_seq(rp[m].cs, m == 1);
+            // recorded, not run: counted at every replay instead
+            rp[m].kernels = g_kernel_launches - before;
+            g_kernel_launches = before;
             cudaGraph_t gr = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(rp[m].cs, &gr);
             rp[m].graph = gr;
@@ -863,8 +873,12 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         if (trace && sw > 0)
             CD_CUDA(launch_features(L.off, L.K, la, L.Sigma, L.size, L.two_m, moved_last, since_move, attach, true,
                                     L.n, x, s));
-        if (rp[use_mask ? 1 : 0].exec) CD_CUDA(cudaGraphLaunch(rp[use_mask ? 1 : 0].exec, s));
-        else CD_TRY(sweep_seq(s, use_mask));
+        if (rp[use_mask ? 1 : 0].exec) {
+            CD_CUDA(cudaGraphLaunch(rp[use_mask ? 1 : 0].exec, s));
+            note_launch(rp[use_mask ? 1 : 0].kernels);
+        } else {
+            CD_TRY(sweep_seq(s, use_mask));
+        }
         HostGlobals hg;
         if (trace && sw > 0) {
             const double r = trace->rate < 0 ? 0 : (trace->rate > 1 ? 1 : trace->rate);
@@ -1091,6 +1105,7 @@ const char* cd_strerror(int code) {
 int cd_last_stats(cd_stats* out) {
     if (!out) return CD_EINVAL;
     *out = g_stats;
+    out->kernel_launches = g_kernel_launches;
     return CD_OK;
 }
 

@@ -82,7 +82,11 @@ int64_t pack_tiles(const PackGraph& p) {
 cudaError_t launch_pack(const PackGraph* pg, const int64_t* tstart, int G, int64_t tiles, int64_t* uoff,
                         int32_t* ucols, uint32_t* uw, uint32_t* gid, uint32_t* lid, int64_t n_total,
                         int64_t nnz_total, Globals* glob, cudaStream_t s) {
-    if (tiles > 0) k_pack<<<(unsigned)tiles, 256, 0, s>>>(pg, tstart, G, uoff, ucols, uw, gid, lid, glob);
+    if (tiles > 0) {
+        note_launch();
+        k_pack<<<(unsigned)tiles, 256, 0, s>>>(pg, tstart, G, uoff, ucols, uw, gid, lid, glob);
+    }
+    note_launch();
     k_set_i64<<<1, 1, 0, s>>>(uoff + n_total, nnz_total);  // closing offset
     return cudaGetLastError();
 }
@@ -108,7 +112,10 @@ __global__ void k_graph_two_m(const uint64_t* __restrict__ K, const int64_t* __r
 
 cudaError_t launch_graph_two_m(const uint64_t* K, const int64_t* vb, const int64_t* nv, int G,
                                unsigned long long* two_m_g, cudaStream_t s) {
-    if (G > 0) k_graph_two_m<<<G, 256, 0, s>>>(K, vb, nv, two_m_g);
+    if (G > 0) {
+        note_launch();
+        k_graph_two_m<<<G, 256, 0, s>>>(K, vb, nv, two_m_g);
+    }
     return cudaGetLastError();
 }
 
@@ -141,8 +148,11 @@ cudaError_t launch_batch_converge(int G, const unsigned long long* two_m_g, cons
                                   const unsigned long long* g_gain_lo, const unsigned long long* g_gain_hi,
                                   double tol, int64_t max_sweeps, uint32_t* gsweeps, uint8_t* gdone, Globals* glob,
                                   cudaStream_t s) {
-    if (G > 0) k_batch_converge<<<(G + 255) / 256, 256, 0, s>>>(G, two_m_g, g_moved, g_gain_lo, g_gain_hi, tol,
-                                                               max_sweeps, gsweeps, gdone, glob);
+    if (G > 0) {
+        note_launch();
+        k_batch_converge<<<(G + 255) / 256, 256, 0, s>>>(G, two_m_g, g_moved, g_gain_lo, g_gain_hi, tol,
+                                                         max_sweeps, gsweeps, gdone, glob);
+    }
     return cudaGetLastError();
 }
 
@@ -154,7 +164,10 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ x, const int64_t* __re
 }
 
 cudaError_t launch_gather_u32(const uint32_t* x, const int64_t* idx, int G, uint32_t* out, cudaStream_t s) {
-    if (G > 0) k_gather_u32<<<(G + 255) / 256, 256, 0, s>>>(x, idx, G, out);
+    if (G > 0) {
+        note_launch();
+        k_gather_u32<<<(G + 255) / 256, 256, 0, s>>>(x, idx, G, out);
+    }
     return cudaGetLastError();
 }
 
@@ -165,7 +178,10 @@ __global__ void k_gather_i64(const int64_t* __restrict__ x, const int64_t* __res
 }
 
 cudaError_t launch_gather_i64(const int64_t* x, const int64_t* idx, int count, int64_t* out, cudaStream_t s) {
-    if (count > 0) k_gather_i64<<<(count + 255) / 256, 256, 0, s>>>(x, idx, count, out);
+    if (count > 0) {
+        note_launch();
+        k_gather_i64<<<(count + 255) / 256, 256, 0, s>>>(x, idx, count, out);
+    }
     return cudaGetLastError();
 }
 
@@ -190,7 +206,10 @@ __global__ void k_batch_labels(const uint32_t* __restrict__ top, const uint32_t*
 
 cudaError_t launch_batch_labels(const uint32_t* top, const uint32_t* gid, int64_t n, int G, const int64_t* vb0,
                                 const int64_t* cb, uint32_t* loc, uint32_t* qlab, cudaStream_t s) {
-    if (n > 0) k_batch_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(top, gid, n, G, vb0, cb, loc, qlab);
+    if (n > 0) {
+        note_launch();
+        k_batch_labels<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(top, gid, n, G, vb0, cb, loc, qlab);
+    }
     return cudaGetLastError();
 }
 
@@ -241,7 +260,10 @@ __global__ void k_batch_modularity(const int64_t* __restrict__ off, const int32_
 cudaError_t launch_batch_modularity(const int64_t* off, const int32_t* cols, const uint32_t* w,
                                     const uint32_t* labels, const uint64_t* Sigma, const int64_t* vb,
                                     const int64_t* nv, int G, unsigned long long* acc, cudaStream_t s) {
-    if (G > 0) k_batch_modularity<<<dim3(G, 16), 256, 0, s>>>(off, cols, w, labels, Sigma, vb, nv, acc);
+    if (G > 0) {
+        note_launch();
+        k_batch_modularity<<<dim3(G, 16), 256, 0, s>>>(off, cols, w, labels, Sigma, vb, nv, acc);
+    }
     return cudaGetLastError();
 }
 

@@ -11,6 +11,12 @@ namespace cdk {
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // key of a never-used sketch slot
 constexpr int kBlock = 256;               // threads per block of the sweep kernels
 
+// Kernels launched on this host thread since the current API call began
+// (cd_stats.kernel_launches); every launch site calls note_launch() as it
+// launches.
+extern thread_local int64_t g_kernel_launches;
+inline void note_launch(int64_t count = 1) { g_kernel_launches += count; }
+
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 

@@ -262,6 +262,7 @@ cudaError_t launch_features(const int64_t* off, const uint64_t* K, const uint32_
                             const uint8_t* since_move, const float* attach, bool attach_raw, int64_t n, void* x,
                             cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_features<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, K, labels, Sigma, size, two_m, moved_last,
                                                            since_move, attach, attach_raw, n,
                                                            static_cast<__half*>(x));
@@ -273,6 +274,7 @@ cudaError_t launch_propose(const int64_t* off, const uint64_t* K, const uint32_t
                            const uint8_t* since_move, const float* attach, int64_t n, const float* param, float thr,
                            uint8_t* active, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_propose<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, K, labels, Sigma, size, two_m, moved_last, since_move,
                                                           attach, n, param, thr, active);
     return cudaGetLastError();
@@ -281,6 +283,7 @@ cudaError_t launch_propose(const int64_t* off, const uint64_t* K, const uint32_t
 cudaError_t launch_mlp_forward(const void* x, int64_t n, const float* param, float* p, uint8_t* active, float thr,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_mlp_forward<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const __half*>(x), n, param, p, active,
                                                               thr);
     return cudaGetLastError();
@@ -294,12 +297,15 @@ cudaError_t launch_mlp_grad(const void* x, const uint8_t* y, int64_t n, const fl
                             float* loss_partial, float* grad, float* loss, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int64_t nb = mlp_grad_blocks(n);
+    note_launch();
     k_mlp_grad<<<(unsigned)nb, 256, 0, s>>>(static_cast<const __half*>(x), y, n, param, partial, loss_partial);
+    note_launch();
     k_mlp_grad_sum<<<1, 352, 0, s>>>(partial, loss_partial, nb, n, grad, loss);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float* param, const float* grad, float* m1, float* m2, int step, float lr, cudaStream_t s) {
+    note_launch();
     k_adam<<<1, 352, 0, s>>>(param, grad, m1, m2, step, lr);
     return cudaGetLastError();
 }
@@ -307,12 +313,14 @@ cudaError_t launch_adam(float* param, const float* grad, float* m1, float* m2, i
 cudaError_t launch_move_state(const uint32_t* before, const uint32_t* after, int64_t n, uint8_t* moved_last,
                               uint8_t* since_move, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_move_state<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(before, after, n, moved_last, since_move);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mark_neighbours(const int64_t* off, const int32_t* cols, const uint32_t* movers,
                                    const Globals* glob, uint8_t* active, cudaStream_t s) {
+    note_launch();
     k_mark_neighbours<<<152 * 16, 128, 0, s>>>(off, cols, movers, glob, active);
     return cudaGetLastError();
 }
@@ -343,6 +351,7 @@ __global__ void k_trace_write(const __half* __restrict__ x, const uint8_t* __res
 cudaError_t launch_trace_flags(const int64_t* off, int64_t n, int sweep, uint32_t thr32, uint32_t* flags,
                                cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_trace_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, n, sweep, thr32, flags);
     return cudaGetLastError();
 }
@@ -350,6 +359,7 @@ cudaError_t launch_trace_flags(const int64_t* off, int64_t n, int sweep, uint32_
 cudaError_t launch_trace_write(const void* x, const uint8_t* moved_last, const uint32_t* flags, const uint32_t* pos,
                                int64_t n, int64_t base, void* xo, uint8_t* yo, int64_t cap, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    note_launch();
     k_trace_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(static_cast<const __half*>(x), moved_last, flags, pos,
                                                               n, base, static_cast<__half*>(xo), yo, cap);
     return cudaGetLastError();

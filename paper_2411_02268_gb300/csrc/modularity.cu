@@ -68,8 +68,10 @@ cudaError_t launch_modularity(const int64_t* off, const int32_t* cols, const uin
     if (e != cudaSuccess) return e;
     if (nnz > 0) {
         const int64_t warps = (nnz + kQTile - 1) / kQTile;
+        note_launch();
         k_sigma_in<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, cols, w, labels, n, nnz, glob);
     }
+    note_launch();
     k_sum_sq<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const unsigned long long*)Sigma_scratch, n, glob);
     return cudaGetLastError();
 }

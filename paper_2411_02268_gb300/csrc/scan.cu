@@ -84,8 +84,11 @@ cudaError_t launch_exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t
                                       cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
     int64_t nt = scan_tiles(n);
+    note_launch();
     k_tile_sums<uint32_t, unsigned long long><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_scratch);
+    note_launch();
     k_scan_sums<unsigned long long><<<1, kScanThreads, 0, s>>>(tile_scratch, nt, total_dev);
+    note_launch();
     k_tile_scan<uint32_t, unsigned long long, uint32_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_scratch,
                                                                                            out);
     return cudaGetLastError();
@@ -96,8 +99,11 @@ cudaError_t launch_exclusive_scan_u32_to_i64(const uint32_t* in, int64_t* out, i
                                              cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
     int64_t nt = scan_tiles(n);
+    note_launch();
     k_tile_sums<uint32_t, unsigned long long><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_scratch);
+    note_launch();
     k_scan_sums<unsigned long long><<<1, kScanThreads, 0, s>>>(tile_scratch, nt, total_dev);
+    note_launch();
     k_tile_scan<uint32_t, unsigned long long, int64_t><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_scratch,
                                                                                           out);
     return cudaGetLastError();

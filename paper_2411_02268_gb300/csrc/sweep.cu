@@ -59,9 +59,13 @@ cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int
                            uint64_t* K, Globals* glob, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(K, 0, sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) k_check_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, n, nnz, glob);
+    if (n > 0) {
+        note_launch();
+        k_check_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(off, n, nnz, glob);
+    }
     if (nnz == 0) return cudaGetLastError();
     const int64_t warps = (nnz + kDegTile - 1) / kDegTile;
+    note_launch();
     k_degrees<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(off, w, n, nnz, (unsigned long long*)K, glob);
     return cudaGetLastError();
 }
@@ -210,6 +214,7 @@ cudaError_t launch_row_sums(const int64_t* off, const uint32_t* w, int64_t n, in
     bt.bbegin[bt.nb] = blk;
     (void)n;
     if (blk == 0) return cudaSuccess;
+    note_launch();
     k_row_sums<<<(unsigned)blk, kBlock, 0, s>>>(off, w, nnz, verts, bt, (unsigned long long*)K, glob);
     return cudaGetLastError();
 }
@@ -222,6 +227,7 @@ cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, 
         if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), s);
     }
     if (e != cudaSuccess || n == 0) return e;
+    note_launch();
     k_totals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(labels, (const unsigned long long*)K, n,
                                                           (unsigned long long*)Sigma, size, glob);
     return cudaGetLastError();
@@ -363,6 +369,7 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
     if (nkeys > kMaxKeys) return cudaErrorInvalidValue;
     if (n == 0) return cudaMemsetAsync(bucket_starts, 0, sizeof(int64_t) * (nkeys + 1), s);
     int64_t ntiles = bucket_tiles(n);
+    note_launch();
     k_bucket_count<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, labels_in, tile_counts, ntiles,
                                                      glob);
     const int64_t m = ntiles * nkeys;
@@ -371,10 +378,13 @@ cudaError_t launch_bucket(const int64_t* off, int64_t n, int64_t nnz, const Buck
         cudaError_t e = launch_exclusive_scan_u32(tile_counts, tile_offsets, m, scan_scratch, &glob->count, s);
         if (e != cudaSuccess) return e;
     } else {
+        note_launch();
         k_scan_small<<<1, 1024, 0, s>>>(tile_counts, tile_offsets, m, &glob->count);
     }
+    note_launch();
     k_bucket_scatter<<<(unsigned)ntiles, 256, 0, s>>>(off, n, nnz, bt, colors, cid, tile_offsets, ntiles, verts,
                                                       labels_in, labels_out);
+    note_launch();
     k_bucket_starts<<<1, 256, 0, s>>>(tile_offsets, ntiles, nkeys, &glob->count, bucket_starts);
     return cudaGetLastError();
 }
@@ -470,14 +480,17 @@ cudaError_t launch_compact(const uint32_t* verts, int64_t m, const uint8_t* acti
     if (colors < 1 || colors > 32) return cudaErrorInvalidValue;
     if (m > 0) {
         const unsigned g = (unsigned)((m + 255) / 256);
+        note_launch();
         k_active_flags<<<g, 256, 0, s>>>(verts, m, active, flags);
         cudaError_t e = launch_exclusive_scan_u32(flags, pos, m, tiles, total, s);
         if (e != cudaSuccess) return e;
+        note_launch();
         k_active_scatter<<<g, 256, 0, s>>>(verts, m, flags, pos, cverts);
     } else {
         cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
+    note_launch();
     k_active_ranges<<<1, 32, 0, s>>>(starts, m, pos, total, bt, colors, dr);
     return cudaGetLastError();
 }
@@ -512,6 +525,7 @@ cudaError_t launch_commit(const uint32_t* movers, uint32_t* labels, const uint32
     if (n == 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
+    note_launch();
     k_commit<<<(unsigned)blocks, 256, 0, s>>>(movers, labels, labels_out, (const unsigned long long*)K,
                                               (unsigned long long*)Sigma, size, glob);
     return cudaGetLastError();

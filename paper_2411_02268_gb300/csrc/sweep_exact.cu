@@ -292,6 +292,7 @@ cudaError_t launch_exact_group(const SweepArgs& a, int bucket, int G, uint32_t T
     cudaError_t e = cudaFuncSetAttribute(k_sweep_exact_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_sweep_exact_group<<<(unsigned)((nv + groups - 1) / groups), kBlock, smem, s>>>(a, bucket, G, T);
     return cudaGetLastError();
 }
@@ -304,6 +305,7 @@ cudaError_t launch_exact_block(const SweepArgs& a, int bucket, uint32_t T_smem, 
     cudaError_t e = cudaFuncSetAttribute(k_sweep_exact_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_sweep_exact_block<<<(unsigned)nv, kBlock, smem, s>>>(a, bucket, T_smem, gkeys, gvals, table_off);
     return cudaGetLastError();
 }
@@ -311,6 +313,7 @@ cudaError_t launch_exact_block(const SweepArgs& a, int bucket, uint32_t T_smem, 
 cudaError_t launch_exact_table_sizes(const SweepArgs& a, int bucket, int64_t* sizes, cudaStream_t s) {
     int64_t nv = a.bt.vbegin[bucket + 1] - a.bt.vbegin[bucket];
     if (nv == 0) return cudaSuccess;
+    note_launch();
     k_exact_table_sizes<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(a, bucket, sizes);
     return cudaGetLastError();
 }

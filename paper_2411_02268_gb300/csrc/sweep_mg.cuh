@@ -1013,6 +1013,7 @@ __global__ void __launch_bounds__(kBlock, (K >= 16 || sizeof(VT) == 8) ? 2 : 4) 
 template <int K>
 cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStream_t s) {
     if (nblocks == 0) return cudaSuccess;
+    note_launch();  // one of the two branches launches
     if (wide) k_agg_mg<K, unsigned long long><<<(unsigned)nblocks, kBlock, 0, s>>>(g);
     else k_agg_mg<K, uint32_t><<<(unsigned)nblocks, kBlock, 0, s>>>(g);
     return cudaGetLastError();
@@ -1027,6 +1028,7 @@ cudaError_t launch_k_mode(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
             cudaFuncSetAttribute(k_sweep_mg<K, VT, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }
+    note_launch();
     k_sweep_mg<K, VT, U><<<(unsigned)nblocks, kBlock, dyn, s>>>(a);
     return cudaGetLastError();
 }

@@ -48,7 +48,7 @@ int main(void) {
   printf("csr %zu %zu %zu\n", sizeof(cd_csr), offsetof(cd_csr, weights), offsetof(cd_csr, memory));
   printf("sched %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes));
   printf("params %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors), offsetof(cd_params, one_scan), offsetof(cd_params, capture));
-  printf("stats %zu %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, entries_scanned), offsetof(cd_stats, cuda_error));
+  printf("stats %zu %zu %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, entries_scanned), offsetof(cd_stats, cuda_error), offsetof(cd_stats, kernel_launches));
   printf("mlp %zu %zu\n", sizeof(cd_mlp), offsetof(cd_mlp, b2));
   printf("parts %zu\n", sizeof(cd_modularity_parts));
   printf("tune %zu %zu %zu %zu\n", sizeof(cd_tune_report), offsetof(cd_tune_report, q_mean), offsetof(cd_tune_report, trials), offsetof(cd_tune_report, chosen));
@@ -62,7 +62,7 @@ int main(void) {
         f"csr {C.sizeof(cd.CSR)} {cd.CSR.weights.offset} {cd.CSR.memory.offset}",
         f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset}",
         f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset} {cd.Params.one_scan.offset} {cd.Params.capture.offset}",
-        f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.entries_scanned.offset} {cd.Stats.cuda_error.offset}",
+        f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.entries_scanned.offset} {cd.Stats.cuda_error.offset} {cd.Stats.kernel_launches.offset}",
         f"mlp {C.sizeof(cd.MLP)} {cd.MLP.b2.offset}",
         f"parts {C.sizeof(cd.ModularityParts)}",
         f"tune {C.sizeof(cd.TuneReport)} {cd.TuneReport.q_mean.offset} {cd.TuneReport.trials.offset} {cd.TuneReport.chosen.offset}",

@@ -64,11 +64,15 @@ def test_batched_equals_single_runs(env, graphs, k):
     cd, torch = env
     dev = [cd.Graph.to_device(g) for g in graphs]
     ref = single_runs(cd, dev, cd.make_params(k=k))
+    launches = []
     for capture in (True, False):
         labs, q, sw = cd.cd_louvain_batched(dev, cd.make_params(k=k, capture=capture))
         check_equal(cd, graphs, labs, q, sw, ref)
+        launches.append(cd.cd_last_stats().kernel_launches)
     st = cd.cd_last_stats()
     assert st.passes >= 2 and st.sweeps >= max(r[2] for r in ref) // 2
+    # a graph replay counts the kernels recorded in it: the same total as launching them
+    assert launches[0] == launches[1] > 0
 
 
 @pytest.mark.parametrize("opts", [dict(max_passes=1), dict(max_sweeps=2), dict(colors=1),

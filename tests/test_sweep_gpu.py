@@ -174,6 +174,16 @@ def test_host_memory_matches_device(env):
     check(cd, torch, g, lab, oracle.MODE_LPA, 8, host=True)
 
 
+def test_sweep_counts_its_kernel_launches(env):
+    """One sweep from singletons on a small graph launches seven kernels: the
+    bucketing (count, single-block scan, scatter, starts), row sums, totals and
+    the sweep."""
+    cd, torch = env
+    g = GRAPHS["sbm10k"]()
+    gpu_sweep(cd, torch, g, np.arange(g.n, dtype=np.uint32), oracle.MODE_LOUVAIN, 8)
+    assert cd.cd_last_stats().kernel_launches == 7
+
+
 def test_wide_sketch_values(env):
     """Weighted degrees above 2^32 switch the sketch to 64-bit values."""
     cd, torch = env
