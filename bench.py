@@ -206,6 +206,17 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: int, dist, device) -> int:
+    """The ranks' values added up (whole-job counts); the value itself with one
+    process."""
+    if dist is None:
+        return int(value)
+    import torch
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
 def lpt_shards(sizes, world: int):
     """Longest-processing-time assignment of items to `world` ranks: items in
     descending size (ties by index) each go to the least-loaded rank (ties to
@@ -504,6 +515,7 @@ def main():
         if dist:
             dist.barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, f"cuda:{local}")
+    all_launches = sum_over_ranks(all_launches, dist, f"cuda:{local}")  # every rank's kernels
     ms_step = ms / args.steps
     gteps = g.nnz * args.steps * world / (ms * 1e-3) / 1e9
     scratch = cd.cd_last_stats().scratch_bytes

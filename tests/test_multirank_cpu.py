@@ -1,6 +1,7 @@
 """The multi-rank path of bench.py on CPU (gloo, world size 2): the slowest
-rank's time is what every rank reports, and the batch is shared out by LPT
-so that every graph goes to exactly one rank."""
+rank's time is what every rank reports, launch counts add up over the
+ranks, and the batch is shared out by LPT so that every graph goes to
+exactly one rank."""
 import itertools
 import os
 import socket
@@ -25,14 +26,15 @@ def _rank_main(rank, world, port, out):
     try:
         local = [3.5, 7.25][rank]
         got = bench.max_over_ranks(local, dist, "cpu")
+        launches = bench.sum_over_ranks([9, 11][rank], dist, "cpu")
         sizes = [5, 1, 9, 3, 3, 8, 2]
         shard = bench.lpt_shards(sizes, world)[rank]
-        out.put((rank, got, shard))
+        out.put((rank, got, shard, launches))
     finally:
         dist.destroy_process_group()
 
 
-def test_two_ranks_max_time_and_disjoint_shards():
+def test_two_ranks_max_time_summed_launches_and_disjoint_shards():
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -45,6 +47,7 @@ def test_two_ranks_max_time_and_disjoint_shards():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert [r[1] for r in res] == [7.25, 7.25]
+    assert [r[3] for r in res] == [20, 20]
     shards = [r[2] for r in res]
     assert sorted(itertools.chain(*shards)) == list(range(7))
 
