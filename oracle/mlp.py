@@ -72,3 +72,26 @@ def gradients(x, y, W1, b1, w2, b2):
 def to_half(a):
     """Round to float16 and back (what the GPU kernels read)."""
     return np.asarray(a, dtype=np.float16).astype(np.float64)
+
+
+def adam_step(params, grads, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, "Adam: A Method for Stochastic
+    Optimization", ICLR 2015, Algorithm 1), elementwise over flat float64
+    arrays: the biased first and second moment estimates
+    m1 <- beta1 m1 + (1 - beta1) g and m2 <- beta2 m2 + (1 - beta2) g^2, their
+    bias-corrected forms m1 / (1 - beta1^t) and m2 / (1 - beta2^t) for step
+    t >= 1, and the parameter step -lr * m1_hat / (sqrt(m2_hat) + eps).
+    Returns new (params, m1, m2); the inputs are not modified."""
+    g = np.asarray(grads, dtype=np.float64)
+    m1 = beta1 * np.asarray(m1, dtype=np.float64) + (1.0 - beta1) * g
+    m2 = beta2 * np.asarray(m2, dtype=np.float64) + (1.0 - beta2) * g * g
+    m1_hat = m1 / (1.0 - beta1 ** step)
+    m2_hat = m2 / (1.0 - beta2 ** step)
+    params = np.asarray(params, dtype=np.float64) - lr * m1_hat / (np.sqrt(m2_hat) + eps)
+    return params, m1, m2
+
+
+def flatten(W1, b1, w2, b2):
+    """The parameters in the library's layout: W1 row by row, b1, w2, b2."""
+    return np.concatenate([np.asarray(W1, dtype=np.float64).reshape(-1), np.asarray(b1, dtype=np.float64),
+                           np.asarray(w2, dtype=np.float64), [float(b2)]])

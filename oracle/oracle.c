@@ -76,59 +76,84 @@ void or_modularity_parts(int64_t n, const int64_t* off, const int32_t* cols, con
 }
 
 /* ---------------------------------------------------------------------------
- * Weighted Misra-Gries sketch, Algorithm 1 (Appendix A.1).
+ * Weighted Misra-Gries sketch, Algorithm 1 (Appendix A.1), stated as a rule.
  *
- * keys[k], vals[k]; a slot with value 0 is empty.  The initial state is
- * keys = EMPTY_KEY, vals = 0.  One update with community c and weight w:
- *   1. add w to every slot whose key is c;
- *   2. if some slot's key is c (live or zeroed), stop;
- *   3. else put (c, w) into the empty slot with the largest index;
- *   4. else subtract w from every slot, clamping at 0 (the new key is dropped).
- * Unconditional variant (Section 4.1, unconditional subtraction): when c
- * is not present, subtract w (clamped) from every slot first, then insert
- * into the largest-index empty slot if one exists.  uncond = 2 selects the
- * weighted Misra-Gries summary of the literature instead (below).
+ * A sketch is k slots (keys[p], vals[p]); a slot whose value is 0 is free,
+ * and a free slot keeps whatever key it last held.  The initial state is
+ * keys = EMPTY_KEY, vals = 0.  Feeding (c, w):
+ *   - if some slot holds the key c, that slot gains w (a freed slot that
+ *     still holds c comes back to life);
+ *   - otherwise the paper's conditional rule takes the free slot with the
+ *     largest index for (c, w), and when there is none it lowers every value
+ *     by w (never below 0) and forgets c.
+ * uncond = 1 (Section 4.1, unconditional subtraction): a c that no slot holds
+ * first lowers every value by w (never below 0), then takes the free slot
+ * with the largest index if one exists.  uncond = 2 selects the weighted
+ * Misra-Gries summary of the literature instead (below).
+ * Keys are never duplicated: c is placed only when no slot holds it.
  * ------------------------------------------------------------------------- */
+static int slot_holding(const uint32_t* keys, int k, uint32_t c) {
+    for (int p = 0; p < k; ++p)
+        if (keys[p] == c) return p;
+    return -1;
+}
+
+static int largest_free_slot(const uint64_t* vals, int k) {
+    for (int p = k - 1; p >= 0; --p)
+        if (vals[p] == 0) return p;
+    return -1;
+}
+
+static void lower_all(uint64_t* vals, int k, uint64_t by) {
+    for (int p = 0; p < k; ++p) vals[p] = vals[p] > by ? vals[p] - by : 0;
+}
+
+static uint64_t smallest_value(const uint64_t* vals, int k) {
+    uint64_t m = vals[0];
+    for (int p = 1; p < k; ++p)
+        if (vals[p] < m) m = vals[p];
+    return m;
+}
+
 void or_sketch_update(uint32_t* keys, uint64_t* vals, int k, uint32_t c, uint64_t w, int uncond) {
-    int has = 0;
-    for (int p = 0; p < k; ++p) {
-        if (keys[p] == c) { vals[p] += w; has = 1; }
-    }
-    if (has) return;
-    if (uncond == 2) {
-        /* the weighted Misra-Gries summary of the literature (not the paper's
-         * rule): a free slot takes (c, w); otherwise every slot loses
-         * d = min(w, smallest value) and what is left of w, if anything, goes
-         * into the largest-index slot that fell to 0 */
-        int e = -1;
-        for (int p = 0; p < k; ++p)
-            if (vals[p] == 0) e = p;
-        if (e >= 0) { keys[e] = c; vals[e] = w; return; }
-        uint64_t m = vals[0];
-        for (int p = 1; p < k; ++p)
-            if (vals[p] < m) m = vals[p];
-        const uint64_t d = w < m ? w : m;
-        for (int p = 0; p < k; ++p) vals[p] -= d;
-        if (w > d) {
-            for (int p = 0; p < k; ++p)
-                if (vals[p] == 0) e = p;
-            keys[e] = c;
-            vals[e] = w - d;
-        }
+    const int held = slot_holding(keys, k, c);
+    if (held >= 0) {
+        vals[held] += w;
         return;
     }
-    if (uncond) {
-        for (int p = 0; p < k; ++p) vals[p] = vals[p] > w ? vals[p] - w : 0;
+    int f;
+    switch (uncond) {
+        case 0: /* Algorithm 1 */
+            f = largest_free_slot(vals, k);
+            if (f < 0) {
+                lower_all(vals, k, w);
+                return;
+            }
+            break;
+        case 1: /* unconditional subtraction */
+            lower_all(vals, k, w);
+            f = largest_free_slot(vals, k);
+            if (f < 0) return;
+            break;
+        default: {
+            /* the weighted Misra-Gries summary of the literature (not the
+             * paper's rule): with no free slot every value drops by
+             * d = min(w, smallest value) and whatever is left of w, if
+             * anything, is placed in the largest-index slot that freed up */
+            f = largest_free_slot(vals, k);
+            if (f < 0) {
+                const uint64_t m = smallest_value(vals, k);
+                const uint64_t d = w < m ? w : m;
+                lower_all(vals, k, d);
+                if (w == d) return;
+                w -= d;
+                f = largest_free_slot(vals, k);
+            }
+            break;
+        }
     }
-    int e = -1;
-    for (int p = 0; p < k; ++p)
-        if (vals[p] == 0) e = p;
-    if (e >= 0) {
-        keys[e] = c;
-        vals[e] = w;
-    } else if (!uncond) {
-        for (int p = 0; p < k; ++p) vals[p] = vals[p] > w ? vals[p] - w : 0;
-    }
+    keys[f] = c;
+    vals[f] = w;
 }
 
 /* merge(A, B): every live slot of B, in slot order, is fed to A as one

@@ -1084,6 +1084,10 @@ void record_cuda_error(cudaError_t e) {
     std::snprintf(g_stats.cuda_error, sizeof(g_stats.cuda_error), "%s", cudaGetErrorString(e));
     cudaGetLastError();
 }
+// For entry points defined in other files: start a call's statistics, and
+// record the modularity it computed.
+void begin_call_stats() { reset_stats(); }
+void record_modularity(double q) { g_stats.modularity = q; }
 }  // namespace cdk
 
 extern "C" {

@@ -11,6 +11,8 @@
 
 namespace cdk {
 void record_cuda_error(cudaError_t e);
+void begin_call_stats();
+void record_modularity(double q);
 }
 
 using namespace cdk;
@@ -62,6 +64,7 @@ int fail(cudaError_t e) {
 
 extern "C" int cd_modularity_noalloc(const cd_csr* g, const uint32_t* labels, void* stream, double* q_out,
                                      cd_modularity_parts* parts) {
+    begin_call_stats();
     if (!g || !labels) return CD_EINVAL;
     if (g->memory != CD_MEM_DEVICE) return CD_EINVAL;
     if (g->n < 0 || g->nnz < 0 || !g->offsets || (g->nnz > 0 && (!g->cols || !g->weights))) return CD_EINVAL;
@@ -102,6 +105,7 @@ extern "C" int cd_modularity_noalloc(const cd_csr* g, const uint32_t* labels, vo
         parts->sum_sq_hi = h.sq_hi;
         parts->two_m = h.two_m;
     }
+    record_modularity(q);
     if (q_out) *q_out = q;
     return CD_OK;
 }

@@ -4,10 +4,13 @@ exactly the labels, modularity and sweep count of cd_louvain on that graph
 alone (same parameters) -- MG sketches (the union keeps each graph's stream
 partition), the exact hashtable (including rows too long for shared
 memory), CUDA-graph replay on and off, host and device inputs, degenerate
-graphs (no vertices, no edges)."""
+graphs (no vertices, no edges).  Every graph of the batch is also compared
+with the oracle's Louvain of the same schedule (oracle.louvain_sync), so that a
+mistake shared by the single and the batched paths cannot pass."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2411_02268_gb300 import gen
 
 pytestmark = pytest.mark.gpu
@@ -73,6 +76,23 @@ def test_batched_equals_single_runs(env, graphs, k):
     assert st.passes >= 2 and st.sweeps >= max(r[2] for r in ref) // 2
     # a graph replay counts the kernels recorded in it: the same total as launching them
     assert launches[0] == launches[1] > 0
+
+
+@pytest.mark.parametrize("k", [8, 0, 16])
+def test_batched_equals_oracle(env, graphs, k):
+    """Every graph of the batch against the CPU oracle's Louvain (same
+    default schedule, 8 colour classes): bit-exact labels and the modularity
+    of those labels to 1e-15."""
+    cd, torch = env
+    dev = [cd.Graph.to_device(g) for g in graphs]
+    labs, q, _ = cd.cd_louvain_batched(dev, cd.make_params(k=k))
+    sched = oracle.Schedule(*cd.cd_default_schedule(k).as_lists())
+    for i, g in enumerate(graphs):
+        got = labs[i].cpu().numpy().view(np.uint32) if g.n else np.zeros(0, np.uint32)
+        ref = oracle.louvain_sync(g, k=k, sched=sched, threads=8)
+        assert np.array_equal(got, ref), f"graph {i} ({g.name}): labels differ from the oracle"
+        qr = float(oracle.modularity_fraction(g, ref)) if g.nnz else 0.0
+        assert q[i] == pytest.approx(qr, abs=1e-15), f"graph {i} ({g.name})"
 
 
 @pytest.mark.parametrize("opts", [dict(max_passes=1), dict(max_sweeps=2), dict(colors=1),

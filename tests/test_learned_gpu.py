@@ -71,6 +71,40 @@ def test_forward_and_gradient_match_oracle(env):
     assert loss2 == loss and np.array_equal(np.ctypeslib.as_array(grad2.W1), np.ctypeslib.as_array(grad.W1))
 
 
+def _flat(m):
+    return mlp.flatten(*m.to_numpy())
+
+
+def test_adam_steps_match_oracle(env):
+    """cd_mlp_train's Adam steps against oracle/mlp.py adam_step (Kingma and
+    Ba 2015) fed with the same gradients: one step from the initial model,
+    then a second step from the first step's parameters, at float32
+    tolerance.  (The gradient kernel itself is checked against the oracle's
+    gradient above; Adam divides by |g|, so comparing it on two independently
+    rounded gradients would amplify their rounding for tiny components.)"""
+    import copy
+    cd, torch = env
+    rng = np.random.default_rng(7)
+    m0 = cd.MLP.init(seed=5)
+    x = torch.from_numpy(rng.random((3000, 8)).astype(np.float16)).cuda()
+    y = torch.from_numpy((rng.random(3000) < 0.35).astype(np.uint8)).cuda()
+    lr = 0.02
+    _, g1 = cd.cd_mlp_gradient(x, y, m0)
+    th0 = _flat(m0)
+    th1, s1, s2 = mlp.adam_step(th0, _flat(g1), np.zeros_like(th0), np.zeros_like(th0), 1, lr)
+    m1 = copy.deepcopy(m0)
+    cd.cd_mlp_train(x, y, m1, steps=1, lr=lr)
+    got1 = _flat(m1)
+    assert np.max(np.abs(got1 - th1) / (np.abs(th1) + lr)) < 1e-6
+    assert np.max(np.abs(got1 - th0)) > 0.5 * lr  # the step moved the parameters
+    _, g2 = cd.cd_mlp_gradient(x, y, m1)
+    th2, _, _ = mlp.adam_step(got1, _flat(g2), s1, s2, 2, lr)
+    m2 = copy.deepcopy(m0)
+    cd.cd_mlp_train(x, y, m2, steps=2, lr=lr)
+    got2 = _flat(m2)
+    assert np.max(np.abs(got2 - th2) / (np.abs(th2) + lr)) < 1e-6
+
+
 def trained_model(cd, torch):
     """Train on move traces of the plain method (10k SBM, a small R-MAT and a
     small rewired grid)."""

@@ -431,6 +431,32 @@ def test_lpa_converges_on_cliques():
     assert len(np.unique(lab)) == 4
 
 
+def lpa_one_scan_case():
+    t = load("lpa_one_scan.json")
+    e = np.array(t["edges"])
+    return gen.from_edges(t["n"], e[:, 0], e[:, 1], e[:, 2]), t
+
+
+@pytest.mark.parametrize("sched", ["single", "default"])
+def test_lpa_one_scan_hand_worked(sched):
+    """LPA 1-scan (Section 4.3) against a sweep worked by hand on two stars
+    whose 2-slot sketches are lossy: the 1-scan choice differs from the
+    2-scan one for both centres, one of them because K_{i->d} comes from the
+    sketch (a zeroed slot), not from a second scan."""
+    g, t = lpa_one_scan_case()
+    s = (oracle.Schedule.single_stream() if sched == "single"
+         else oracle.Schedule([2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 16384, 2**62],
+                              [1, 1, 1, 1, 1, 1, 1, 2, 4, 4, 8, 8, 32, 256], 4))
+    lab = np.array(t["labels_in"], dtype=np.uint32)
+    for row, key in ((0, "sketch_row0"), (6, "sketch_row6")):
+        keys, vals = oracle.row_sketch(g, row, lab, t["k"], s)
+        assert keys.tolist() == t[key]["keys"] and vals.tolist() == t[key]["vals"]
+    for one, lk, gk in ((False, "two_scan_labels", "two_scan_gains"), (True, "one_scan_labels", "one_scan_gains")):
+        out, gains = oracle.sweep(g, lab, oracle.MODE_LPA, k=t["k"], uncond=t["subtract"], sched=s, one_scan=one)
+        assert out.tolist() == t[lk]
+        assert oracle.gains_as_ints(gains) == t[gk]
+
+
 def _lowbias32(x: int) -> int:
     x &= 0xFFFFFFFF
     x ^= x >> 16
@@ -617,3 +643,42 @@ def test_mlp_features_definition():
     assert x[:, 1].tolist() == [1, 0, 1] and x[:, 2].tolist() == [0, 3 / 8, 1]
     assert x[1, 3] == np.log2(5) / 24 and x[1, 4] == np.sqrt(12 / 4000) and x[1, 5] == 0.5
     assert x[:, 6].tolist() == [0.0, 0.25, 1.0] and np.all(x[:, 7] == 1.0) and x[0, 5] == 0.0
+
+
+def test_adam_two_steps_by_hand():
+    """Adam (Kingma and Ba 2015, Algorithm 1) on one parameter, worked with
+    fractions: theta0 = 1, lr = 0.1, g1 = 1/2, g2 = -1/4.  Step 1: m = 1/20,
+    v = 1/4000, m_hat = 1/2, v_hat = 1/4, theta1 = 1 - 0.1 (1/2) / (1/2 + 1e-8).
+    Step 2: m = 9/10 * 1/20 - 1/40 = 1/50, v = 999/1000 * 1/4000 + 1/16000 =
+    1249/4000000, m_hat = (1/50) / (19/100) = 2/19, v_hat = (1249/4000000) /
+    (1999/1000000) = 1249/7996, theta2 = theta1 - 0.1 (2/19) / (sqrt(1249/7996)
+    + 1e-8)."""
+    from oracle import mlp
+    p1, m1, m2 = mlp.adam_step([1.0], [0.5], [0.0], [0.0], 1, 0.1)
+    assert m1[0] == pytest.approx(1 / 20, rel=1e-15) and m2[0] == pytest.approx(1 / 4000, rel=1e-12)
+    assert p1[0] == pytest.approx(1 - 0.1 * 0.5 / (0.5 + 1e-8), rel=1e-15)
+    assert abs(p1[0] - 0.900000002) < 1e-15
+    p2, m1, m2 = mlp.adam_step(p1, [-0.25], m1, m2, 2, 0.1)
+    assert m1[0] == pytest.approx(1 / 50, rel=1e-12) and m2[0] == pytest.approx(1249 / 4000000, rel=1e-12)
+    assert abs(p2[0] - 0.8733662987078462) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_adam_step_size_and_scale_invariance(seed):
+    """Two properties the Adam paper states (Section 2.1): the first step
+    moves every parameter by lr in the direction against its gradient
+    (m_hat / sqrt(v_hat) = sign(g) at t = 1, up to eps), and the update is
+    invariant to a rescaling of the gradients (exactly so with eps = 0)."""
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    th = rng.normal(size=20)
+    g = rng.normal(size=20) * 10.0 ** rng.uniform(-3, 2, 20)
+    p1, _, _ = mlp.adam_step(th, g, np.zeros(20), np.zeros(20), 1, 0.01)
+    assert np.allclose(p1 - th, -0.01 * np.sign(g), rtol=1e-5, atol=0)
+    p, m1, m2 = th, np.zeros(20), np.zeros(20)
+    q, n1, n2 = th, np.zeros(20), np.zeros(20)
+    for t in range(1, 6):
+        gt = rng.normal(size=20)
+        p, m1, m2 = mlp.adam_step(p, gt, m1, m2, t, 0.01, eps=0.0)
+        q, n1, n2 = mlp.adam_step(q, 37.5 * gt, n1, n2, t, 0.01, eps=0.0)
+        assert np.allclose(p, q, rtol=1e-12, atol=1e-14)

@@ -334,6 +334,22 @@ def test_lpa_one_scan_parity(env, gname, k):
         assert gain == oracle.gain_total(gains)
 
 
+def test_lpa_one_scan_golden(env):
+    """The hand-worked two-star LPA sweep (k = 2) with and without 1-scan."""
+    import json, os
+    cd, torch = env
+    t = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "lpa_one_scan.json")))
+    e = np.array(t["edges"])
+    g = gen.from_edges(t["n"], e[:, 0], e[:, 1], e[:, 2])
+    lab = torch.from_numpy(np.array(t["labels_in"], dtype=np.int32)).cuda()
+    G = cd.Graph.to_device(g)
+    for one, lk, gk in ((False, "two_scan_labels", "two_scan_gains"), (True, "one_scan_labels", "one_scan_gains")):
+        out, moved, gain = cd.cd_sweep(G, cd.make_params(k=t["k"], one_scan=one), cd.MODE_LPA, lab)
+        assert out.cpu().numpy().tolist() == t[lk]
+        assert moved == sum(1 for x in t[gk] if x > 0)
+        assert gain == sum(t[gk])
+
+
 # ---- large sketches (k = 32, 64: the paper's Leiden uses 64 slots) --------------------
 # These merge inside one warp, so their schedules give a row at most 32 streams.
 BIG_LANES = ([1, 2, 4, 8, 16, 40, 2**62], [1, 2, 4, 8, 16, 32, 32])

@@ -8,6 +8,7 @@ limit.  Kept in its own file, collected last."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2411_02268_gb300 import gen
 
 pytestmark = pytest.mark.gpu
@@ -36,8 +37,14 @@ def test_noalloc_matches_cd_modularity_twice(env):
         dlab = torch.from_numpy(lab.astype(np.uint32).view(np.int32)).cuda()
         q_ref, parts_ref = cd.cd_modularity(G, dlab)
         q, parts = cd.cd_modularity_noalloc(G, dlab)
+        st = cd.cd_last_stats()
         assert parts == parts_ref
         assert q == pytest.approx(q_ref, abs=1e-15)
+        # and directly against the CPU oracle's integer parts of Eq. 1
+        assert parts == oracle.modularity_parts(g, lab.astype(np.uint32))
+        # the call's own statistics, not the previous call's
+        assert st.modularity == q
+        assert 0 < st.kernel_launches <= 4 and st.scratch_bytes == 0
 
 
 def test_noalloc_size_limit_and_memory_kind(env):
