@@ -242,7 +242,7 @@ struct Level {
             t.vbegin[b] = starts[(size_t)p * bt.nb + b];
             t.bbegin[b] = blk;
             int64_t nv = starts[(size_t)p * bt.nb + b + 1] - t.vbegin[b];
-            int Lb = bt.lanes[b];
+            int Lb = threads_per_row(bt, b);
             int vpb = Lb >= kBlock ? 1 : kBlock / Lb;
             blk += (nv + vpb - 1) / vpb;
         }
@@ -272,9 +272,10 @@ int read_globals(Globals* dglob, int64_t* dstarts, int nb, HostGlobals* out, cud
 
 // K, totals from `labels`, buckets by (colour class, row length); reads back
 // 2m, max K and the bucket ranges.
-int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, bool exact,
+int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, int k,
                   const cd_schedule& sched, int colors, Scratch& sc, Globals* dglob, cudaStream_t s,
                   bool singletons = false, cudaEvent_t weights_ready = nullptr) {
+    const bool exact = k == 0;
     const bool fresh = !L.reuse || !L.K;
     if (fresh) {
         CD_TRY(sc.get(&L.K, L.n));
@@ -283,6 +284,7 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, b
         CD_TRY(sc.get(&L.verts, L.n));
     }
     L.bt = exact ? exact_table() : table_from(sched);
+    L.bt.qmul = slot_lanes(k);
     L.colors = colors;
     const int nkeys = colors * L.bt.nb;
     int64_t ntiles = bucket_tiles(L.n);
@@ -729,7 +731,7 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
     if (init) CD_CUDA(cudaMemcpyAsync(la, init, sizeof(uint32_t) * L.n, cudaMemcpyDeviceToDevice, s));
     else CD_CUDA(launch_iota(la, L.n, s));
     const int colors = resolve_colors(p);
-    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s, init == nullptr));
+    CD_TRY(prepare_level(L, la, lb, p->k, sched, colors, sc, dglob, s, init == nullptr));
     const int rule = trace ? 0 : p->skip_rule;
     const bool track = rule != 0 || trace;
     uint8_t *active = nullptr, *moved_last = nullptr, *since_move = nullptr;
@@ -941,7 +943,7 @@ int refine_level(Level& L, const cd_params* p, const uint32_t* bound, const cd_s
     CD_TRY(sc.get(&L.movers, L.n));
     CD_CUDA(launch_iota(la, L.n, s));
     const int colors = resolve_colors(p);
-    CD_TRY(prepare_level(L, la, lb, p->k == 0, sched, colors, sc, dglob, s, true));
+    CD_TRY(prepare_level(L, la, lb, p->k, sched, colors, sc, dglob, s, true));
     const size_t stat_off = offsetof(Globals, moved);
     const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
     CD_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(dglob) + stat_off, 0, stat_len, s));
@@ -1192,7 +1194,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         if (gain_out) { gain_out[0] = 0; gain_out[1] = 0; }
         return CD_OK;
     }
-    CD_TRY(prepare_level(L, lin, lout, p->k == 0, sched, 1, sc, dglob, s, false, host ? side.ev[1] : nullptr));
+    CD_TRY(prepare_level(L, lin, lout, p->k, sched, 1, sc, dglob, s, false, host ? side.ev[1] : nullptr));
     if (host) CD_CUDA(cudaStreamWaitEvent(s, side.ev[2], 0));  // the columns before the sweep
     SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, resolve_colors(p), p->sub_color);
     a.one_scan = p->one_scan;
@@ -1580,7 +1582,7 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
         const size_t stat_len = offsetof(Globals, sigma_in) - stat_off;
         // median time of one full sweep of the batch with schedule sc_try and k
         auto time_sweep = [&](const cd_schedule& st, int k, double* ms_out) -> int {
-            CD_TRY(prepare_level(L, la, lb, k == 0, st, 1, sc, dglob, s, true));
+            CD_TRY(prepare_level(L, la, lb, k, st, 1, sc, dglob, s, true));
             CD_CUDA(launch_graph_two_m(L.K, dvb, dnv, G, two_m_g, s));
             SweepArgs a = make_args(L, la, lb, nullptr, nullptr, dglob, CD_MODE_LOUVAIN, p->subtract);
             a.gid = gid0;

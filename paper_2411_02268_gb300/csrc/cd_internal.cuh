@@ -41,6 +41,7 @@ struct Globals {
 // and is processed by grid blocks [bbegin[b], bbegin[b+1]).
 struct BucketTable {
     int nb;
+    int qmul;  // lanes per stream: k / 8 for the slot form of k >= 32, else 1 (0 reads as 1)
     int lanes[CD_MAX_BUCKETS];
     int64_t deg_max[CD_MAX_BUCKETS];
     int64_t vbegin[CD_MAX_BUCKETS + 1];
@@ -147,6 +148,13 @@ __device__ __forceinline__ bool barred_n(const SweepArgs& a, uint32_t c, uint32_
                                          uint32_t size_c) {
     if (a.mode == CD_MODE_REFINE) return size_c == 1 && (int)color_of(c, a.colors) == a.sub_color;
     return d_single && c > d && size_c == 1;
+}
+
+// Lanes per stream of the MG sweep kernel for sketch size k (the slot form
+// spreads k >= 32 slots over k / 8 lanes), and the threads of one row.
+__host__ __device__ __forceinline__ int slot_lanes(int k) { return k >= 32 ? k / 8 : 1; }
+__host__ __device__ __forceinline__ int threads_per_row(const BucketTable& bt, int b) {
+    return bt.lanes[b] * (bt.qmul > 1 ? bt.qmul : 1);
 }
 
 // Host-side launchers (sweep.cu).

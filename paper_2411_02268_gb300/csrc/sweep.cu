@@ -465,7 +465,7 @@ __global__ void k_active_ranges(const int64_t* __restrict__ starts, int64_t m, c
         const int64_t v0 = at(starts[(int64_t)c * bt.nb + b]), v1 = at(starts[(int64_t)c * bt.nb + b + 1]);
         dr[c].vbegin[b] = v0;
         dr[c].bbegin[b] = blk;
-        const int L = bt.lanes[b];
+        const int L = threads_per_row(bt, b);
         const int vpb = L >= kBlock ? 1 : kBlock / L;
         blk += (v1 - v0 + vpb - 1) / vpb;
     }

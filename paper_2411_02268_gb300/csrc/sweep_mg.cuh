@@ -174,47 +174,6 @@ __device__ __forceinline__ bool decide(const SweepArgs& a, uint32_t i, uint32_t 
     return have;
 }
 
-// decide() for candidate tables in shared memory (large sketches): the same
-// rule over cand[0, K) and acc[0, K), in a loop.
-template <int K, typename VT>
-__device__ __noinline__ bool decide_dyn(const SweepArgs& a, uint32_t i, uint32_t d, const uint32_t* cand,
-                                        const VT* acc, VT kid, uint32_t& best_out, u128& gain_out) {
-    uint32_t best = d;
-    VT best_w = kid;
-    bool have = false;
-    if (a.mode == CD_MODE_LPA) {
-        VT bk = kid;
-#pragma unroll 1
-        for (int p = 0; p < K; ++p) {
-            const uint32_t c = cand[p];
-            if (c == kEmpty) continue;
-            const VT v = acc[p];
-            if (v > kid && (v > bk || (v == bk && c < best))) { best = c; bk = v; have = true; }
-        }
-        gain_out = have ? (u128)(bk - kid) : (u128)0;
-        best_w = bk;
-    } else {
-        const unsigned long long two_m = two_m_of(a, i);
-        const unsigned long long Ki = a.K[i];
-        const unsigned long long Sd = a.Sigma[d];
-        const bool sd1 = a.size[d] == 1;
-        i128 bg = 0;
-#pragma unroll 1
-        for (int p = 0; p < K; ++p) {
-            const uint32_t c = cand[p];
-            if (c == kEmpty) continue;
-            if (barred(a, c, d, sd1)) continue;
-            const i128 g = (i128)two_m * ((i128)acc[p] - (i128)kid) -
-                           (i128)Ki * ((i128)Ki + (i128)a.Sigma[c] - (i128)Sd);
-            if (g > 0 && (g > bg || (g == bg && c < best))) { best = c; bg = g; have = true; best_w = acc[p]; }
-        }
-        gain_out = have ? (u128)bg : (u128)0;
-    }
-    best_out = best;
-    if (a.attach) a.attach[i] = (float)best_w;
-    return have;
-}
-
 // Chunk ch of the CSR: 4 entries, 16-byte aligned.
 struct Chunk {
     int c[4];
@@ -490,136 +449,6 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
 }
 
 // ---------------------------------------------------------------------------
-// Large sketches (k = 32, 64): G <= 32 streams per vertex inside one warp, as
-// group_body, with the merge tree and the candidate tables in a per-warp
-// shared-memory stage (the register form would unroll k x k updates per
-// merge round and hold k more values per lane).  Merge round o: streams
-// [o, 2o) of each group stage their sketch at rows wb/2 + (lane - o) (wb =
-// the group's first lane in the warp) and streams [0, o) feed them slot by
-// slot.  Then the stage holds one candidate table per group; the second
-// scan adds each entry's weight to its candidate's slot with a shared-memory
-// atomic (integer sums: order-independent).
-// ---------------------------------------------------------------------------
-template <int K, typename VT>
-struct WarpStage {
-    struct Merge {
-        uint32_t k[K][16];
-        VT v[K][16];
-        int lossy[16];
-    };
-    struct Tables {
-        uint32_t cand[32][K];
-        VT acc[32][K];
-    };
-    union {
-        Merge m;
-        Tables t;
-    };
-};
-
-template <int G, int K, typename VT, typename U>
-__device__ __forceinline__ Outcome group_body_big(const SweepArgs& a, int64_t vi, bool valid,
-                                                  WarpStage<K, VT>& ws) {
-    const int lane = threadIdx.x & (G - 1);
-    const int wl = threadIdx.x & 31;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (wl & ~(G - 1)));
-    Outcome out{false, 0, 0, 0};
-    uint32_t i = 0, d = 0, bi = 0;
-    int64_t start = 0, end = 0;
-    bool act = valid;
-    if (valid) {
-        i = a.verts[vi];
-        act = vertex_decides(a, i);
-        if (act || a.out_all) d = a.labels[i];
-        if (act) {
-            start = a.off[i];
-            end = a.off[i + 1];
-            if (a.bound) {
-                bi = a.bound[i];
-                if (a.size[d] != 1) act = false;
-            }
-        }
-    }
-    Sketch<K, VT> sk;
-    sk.init();
-    const U unc = mode_of<U>(a);
-    const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
-    const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
-    if (act) scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
-    const int wb = wl & ~(G - 1);
-#pragma unroll 1
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        if (lane >= o && lane < 2 * o) {
-            const int r = wb / 2 + (lane - o);
-#pragma unroll
-            for (int p = 0; p < K; ++p) {
-                ws.m.k[p][r] = sk.key[p];
-                ws.m.v[p][r] = sk.value(p);
-            }
-            ws.m.lossy[r] = sk.lossy;
-        }
-        __syncwarp(gmask);
-        if (lane < o) {
-            const int r = wb / 2 + lane;
-#pragma unroll 1
-            for (int p = 0; p < K; ++p) {
-                const VT v = ws.m.v[p][r];
-                if (v > 0) sk.update(ws.m.k[p][r], v, unc);
-            }
-            sk.lossy |= ws.m.lossy[r] != 0;
-        }
-        __syncwarp(gmask);
-    }
-    __syncwarp();  // every group of the warp has merged: the stage becomes the candidate tables
-    uint32_t* cs = ws.t.cand[wl / G];
-    VT* as = ws.t.acc[wl / G];
-    const bool exact = __shfl_sync(gmask, (int)sk.lossy, 0, G) == 0 || a.one_scan;
-    VT kid = 0;
-    if (lane == 0) {
-#pragma unroll
-        for (int p = 0; p < K; ++p) {
-            const VT v = sk.value(p);
-            const uint32_t kk = v > 0 ? sk.key[p] : kEmpty;
-            cs[p] = kk == d ? kEmpty : kk;
-            as[p] = (exact && kk != d) ? v : (VT)0;  // exact when the sketch never subtracted
-            kid += kk == d ? v : (VT)0;
-        }
-    }
-    __syncwarp(gmask);
-    if (!exact) {
-        kid = 0;
-        uint32_t cand[K];
-#pragma unroll
-        for (int p = 0; p < K; ++p) cand[p] = cs[p];
-        if (act) {
-            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) {
-                kid += c == d ? (VT)w : (VT)0;
-                int m = -1;
-#pragma unroll
-                for (int p = 0; p < K; ++p) m = c == cand[p] ? p : m;
-                if (m >= 0) atomicAdd(&as[m], (VT)w);
-            });
-        }
-#pragma unroll
-        for (int o = G / 2; o >= 1; o >>= 1) kid += __shfl_down_sync(gmask, kid, o, G);
-        __syncwarp(gmask);
-    }
-    if (act && lane == 0) {
-        uint32_t best;
-        u128 g;
-        const bool mv = decide_dyn<K, VT>(a, i, d, cs, as, kid, best, g);
-        a.labels_out[i] = best;
-        out.moved = mv;
-        out.gain = g;
-        out.vertex = i;
-        out.scanned = (uint32_t)(end - start);
-    } else if (valid && !act && lane == 0 && a.out_all) {
-        a.labels_out[i] = d;
-    }
-    return out;
-}
-
-// ---------------------------------------------------------------------------
 // L = 64, 128 or 256 streams per vertex: L/32 warps (a sub-block of the
 // 256-thread block, synchronised by a named barrier).
 // ---------------------------------------------------------------------------
@@ -831,9 +660,14 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs& a, const Outcome
     if (o.moved && a.movers) a.movers[e.base + woff + __popc(mm & ((1u << lane) - 1u))] = o.vertex;
 }
 
-// Shared memory of the sub-block merges (k <= 16; larger sketches use at
-// most 32 streams per row and merge inside one warp).
-struct NoSmem {};
+}  // namespace cdk
+
+#include "sweep_slots.cuh"
+
+namespace cdk {
+
+// Shared memory of the sub-block merges (k <= 16; larger sketches use the
+// slot form of sweep_slots.cuh).
 struct NoTabs {};
 template <int K, typename VT>
 union SmallSketchSmem {
@@ -841,7 +675,7 @@ union SmallSketchSmem {
     typename std::conditional<(K >= 16), PassTwoTabs<VT>, NoTabs>::type t;  // second-scan tables
 };
 template <int K, typename VT>
-using SweepSmem = typename std::conditional<(K <= 16), SmallSketchSmem<K, VT>, NoSmem>::type;
+using SweepSmem = typename std::conditional<(K <= 16), SmallSketchSmem<K, VT>, SlotSmem<VT>>::type;
 
 template <int K, typename VT>
 __device__ __forceinline__ PassTwoTabs<VT>* tabs_of(SmallSketchSmem<K, VT>& sm) {
@@ -851,13 +685,12 @@ __device__ __forceinline__ PassTwoTabs<VT>* tabs_of(SmallSketchSmem<K, VT>& sm) 
 
 template <int K, typename VT>
 constexpr int sweep_min_blocks() {
-    return K >= 32 ? 1 : ((K >= 16 || sizeof(VT) == 8) ? 2 : 4);
+    return K >= 32 ? 4 : ((K >= 16 || sizeof(VT) == 8) ? 2 : 4);
 }
 
 template <int K, typename VT, typename U>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(const SweepArgs a) {
     __shared__ SweepSmem<K, VT> sm;
-    extern __shared__ __align__(16) unsigned char dyn_smem[];  // k >= 32: one WarpStage per warp
     __shared__ EpiSmem esm;
     // Virtual blocks, the longest rows first, so that they start at once and
     // overlap with the many short rows instead of trailing the launch.  A
@@ -887,19 +720,20 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(
         }
         const int L = a.bt.lanes[b];
         const int64_t lb = blk - bb0;
-        const int vpb = L >= kBlock ? 1 : kBlock / L;
-        const int64_t vi = vb0 + lb * vpb + threadIdx.x / L;
+        // threads per row: L streams, each of Q = k/8 lanes for k >= 32
+        const int T = K >= 32 ? L * (K / 8) : L;
+        const int vpb = T >= kBlock ? 1 : kBlock / T;
+        const int64_t vi = vb0 + lb * vpb + threadIdx.x / T;
         const bool valid = vi < vb1;
         Outcome o;
         if constexpr (K >= 32) {
-            WarpStage<K, VT>& ws = reinterpret_cast<WarpStage<K, VT>*>(dyn_smem)[threadIdx.x >> 5];
             switch (L) {  // the host caps L at 32 for these sketch sizes
-                case 1: o = group_body_big<1, K, VT, U>(a, vi, valid, ws); break;
-                case 2: o = group_body_big<2, K, VT, U>(a, vi, valid, ws); break;
-                case 4: o = group_body_big<4, K, VT, U>(a, vi, valid, ws); break;
-                case 8: o = group_body_big<8, K, VT, U>(a, vi, valid, ws); break;
-                case 16: o = group_body_big<16, K, VT, U>(a, vi, valid, ws); break;
-                default: o = group_body_big<32, K, VT, U>(a, vi, valid, ws); break;
+                case 1: o = slot_body<1, K, VT, U>(a, vi, valid, sm); break;
+                case 2: o = slot_body<2, K, VT, U>(a, vi, valid, sm); break;
+                case 4: o = slot_body<4, K, VT, U>(a, vi, valid, sm); break;
+                case 8: o = slot_body<8, K, VT, U>(a, vi, valid, sm); break;
+                case 16: o = slot_body<16, K, VT, U>(a, vi, valid, sm); break;
+                default: o = slot_body<32, K, VT, U>(a, vi, valid, sm); break;
             }
         } else {
             switch (L) {
@@ -1021,15 +855,8 @@ cudaError_t launch_agg_k(const AggArgs& g, bool wide, int64_t nblocks, cudaStrea
 
 template <int K, typename VT, typename U>
 cudaError_t launch_k_mode(const SweepArgs& a, int64_t nblocks, cudaStream_t s) {
-    size_t dyn = 0;
-    if constexpr (K >= 32) {
-        dyn = sizeof(WarpStage<K, VT>) * (kBlock / 32);
-        cudaError_t e =
-            cudaFuncSetAttribute(k_sweep_mg<K, VT, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-    }
     note_launch();
-    k_sweep_mg<K, VT, U><<<(unsigned)nblocks, kBlock, dyn, s>>>(a);
+    k_sweep_mg<K, VT, U><<<(unsigned)nblocks, kBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
