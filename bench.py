@@ -1,17 +1,19 @@
 """Benchmark of the MG-sketch local-moving sweep on one or more GB300s.
 
-One step = one pass of the hot path over the synthetic R-MAT scale-22 graph
-(2^22 vertices, edge factor 16, (a,b,c) = (0.57, 0.19, 0.19), weights in
-[1, 16]; about 128M CSR entries): weighted degrees and degree buckets, then
-one synchronous Louvain sweep with the k = 8 weighted Misra-Gries sketch
-(sketch scan, merge tree, exact second scan, Eq. 2 decision, mover
-statistics), from singleton communities, through the C ABI (cd_sweep).
+One step = one pass of the hot path over the synthetic R-MAT scale-25 graph
+(2^25 vertices, edge factor 16, (a,b,c) = (0.57, 0.19, 0.19), weights in
+[1, 255]; about 1.05G CSR entries, the largest workload that fits one GPU):
+weighted degrees and degree buckets, then one synchronous Louvain sweep with
+the k = 8 weighted Misra-Gries sketch (sketch scan, merge tree, exact second
+scan, Eq. 2 decision, mover statistics), from singleton communities, through
+the C ABI (cd_sweep).  Beside it: the same sweep from the communities of the
+first Louvain pass (a mid-run sweep).
 
 Prints one JSON line (rank 0).  `value` is local-move throughput in GTEPS
 (CSR entries swept per second, all ranks), timed with CUDA events on the
-launching stream; the graph (1 GB) is larger than L2, so no flush is needed
-between steps.  `--impl reference` times the CPU oracle on the host cores on a
-bounded sample of the same workload instead.
+launching stream; the graph (8.6 GB) is larger than L2, so no flush is
+needed between steps.  `--impl reference` times the CPU oracle on the host
+cores on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -30,6 +32,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+
+METRIC = "local-move GTEPS (Louvain, MG k=8 sweep)"
 
 WORKLOADS = {
     "rmat22": dict(desc="R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16], seed 1"),
@@ -55,15 +59,40 @@ def make_graph(name: str):
     raise ValueError(name)
 
 
-def algorithmic_bytes(g, k: int) -> dict:
+# The library's default stream schedule (cd_default_schedule), written out
+# so that the oracle legs never load the CUDA library; a CPU test checks that
+# it equals the library's.
+DEFAULT_DEG_MAX = [2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 16384, 2**63 - 1]
+DEFAULT_LANES = [1, 1, 1, 1, 1, 1, 1, 2, 4, 4, 8, 8, 32, 256]
+
+
+def default_schedule(k: int):
+    """(deg_max, lanes, vec) of the default schedule for sketch size k."""
+    cap = 32 if k >= 32 else 256
+    return list(DEFAULT_DEG_MAX), [min(x, cap) for x in DEFAULT_LANES], 4
+
+
+def algorithmic_bytes(g, k: int, candidates: float = 0.0) -> dict:
     """Bytes one sweep must move at least: per CSR entry cols 4 + w 4 +
     labels[col] 4; per vertex with edges offsets 8 + K 8 + label in 4 +
-    label out 4 + Sigma_d 8 + size 4.  Candidate Sigma_c gathers are not
-    counted (their number is data-dependent), so this is a lower bound."""
+    label out 4 + Sigma_d 8 + size 4; per candidate a vertex evaluates, its
+    Sigma_c 8 (`candidates` = the sweep's total, measured by the library)."""
     deg = np.diff(g.offsets)
     n_active = int(np.count_nonzero(deg))
-    return dict(per_entry=12, per_vertex=36, entries=int(g.nnz), vertices=n_active,
-                bytes=12 * int(g.nnz) + 36 * n_active)
+    return dict(per_entry=12, per_vertex=36, per_candidate=8, entries=int(g.nnz), vertices=n_active,
+                candidates=float(candidates),
+                bytes=12 * int(g.nnz) + 36 * n_active + int(round(8 * candidates)))
+
+
+def workload_config(args, g, world: int) -> dict:
+    """The `config` of the JSON line, identical for both arms."""
+    graph_bytes = 8 * (g.n + 1) + 8 * int(g.nnz)
+    return {"workload": WORKLOADS[args.workload]["desc"], "n": int(g.n), "nnz": int(g.nnz), "k": args.k,
+            "mode": "louvain", "labels": "singletons",
+            "step": "cd_sweep: weighted degrees, degree buckets, one MG-sketch Louvain sweep",
+            "l2": ("inputs larger than L2 (no flush)" if graph_bytes > 129 * 2**20
+                   else "inputs smaller than L2 (not flushed)"),
+            "parallelism": f"replicas{world}"}
 
 
 def kernel_source_hash(k: int = 8) -> str:
@@ -160,8 +189,7 @@ def oracle_sample(g, k: int, seconds: float, threads: int, repeat: bool = True):
     """Times the CPU oracle sweep on a growing random vertex sample until about
     `seconds` of CPU work; returns (entries swept per second, description)."""
     import oracle
-    from paper_2411_02268_gb300 import cd
-    sched = oracle.Schedule(*cd.cd_default_schedule(k).as_lists())
+    sched = oracle.Schedule(*default_schedule(k))
     K = oracle.degrees(g)
     labels = np.arange(g.n, dtype=np.uint32)
     Sig, size = oracle.community_totals(g.n, labels, K)
@@ -277,14 +305,18 @@ def learned_vs_plain(cd, torch, side: int, rmat_scale: int = 0):
     return out
 
 
-def variants_vs_exact(cd, torch, G):
-    """The paper's comparison (Section 5.2-5.4): each method with its MG
-    sketch size against the exact hashtable (k = 0) and weighted Boyer-Moore
-    (k = 1), and the weighted Misra-Gries of the literature (subtract = 2)
-    beside the paper's rule: modularity, wall time of the whole detection
-    (device-resident graph) and peak device scratch; on the bench graph, and
-    Louvain k = 8 against exact on the 10k planted-partition graph (100 blocks, p_in 0.05,
-    p_out 0.0005) and on a rewired 1024 x 1024 grid."""
+def variants_vs_exact(cd, torch, seeds=(1, 2, 3), permuted=True, small=True):
+    """The paper's comparison (Section 5.2-5.4) on the scale-22 R-MAT
+    workload: Louvain, Leiden and LPA with MG sketches of k = 4, 8 and 16
+    slots against the exact hashtable (k = 0), for each seed, plus weighted
+    Boyer-Moore (Louvain k = 1), the weighted Misra-Gries of the literature
+    (Louvain k = 8, subtract = 2), Leiden with the paper's 32 and 64 slots
+    and LPA 1-scan; with `permuted`, the same on the seed-1 graph with
+    randomly permuted vertex ids.  Each run: modularity, wall time of the
+    whole detection (device-resident graph), sweeps, peak device scratch,
+    and Q and time relative to the exact hashtable of the same method.
+    With `small`, Louvain and Leiden on the 10k planted-partition graph and
+    a rewired 1024 x 1024 grid."""
     from paper_2411_02268_gb300 import gen
 
     def one(Gx, method, k, kw):
@@ -298,28 +330,52 @@ def variants_vs_exact(cd, torch, G):
         return {"q": q, "ms": (time.perf_counter() - t) * 1e3, "sweeps": int(st.sweeps),
                 "passes": int(st.passes), "scratch_bytes": int(st.scratch_bytes)}
 
-    def vs(out, a, b):
-        out[a]["q_vs_exact"] = out[a]["q"] / out[b]["q"] if out[b]["q"] else None
-        out[a]["time_vs_exact"] = out[a]["ms"] / out[b]["ms"]
+    def name_of(method, k, kw):
+        return f"{method}_k{k}" + ("_1scan" if kw.get("one_scan") else "") + ("_textbook" if kw.get("subtract") else "")
 
-    runs = [("louvain", 8, {}), ("louvain", 8, {"subtract": 2}), ("louvain", 1, {}), ("louvain", 0, {}),
-            ("leiden", 64, {}), ("leiden", 8, {}), ("leiden", 0, {}),
-            ("lpa", 8, {}), ("lpa", 8, {"one_scan": True}), ("lpa", 0, {})]
-    out = {}
-    for method, k, kw in runs:
-        name = f"{method}_k{k}" + ("_1scan" if kw.get("one_scan") else "") + ("_textbook" if kw.get("subtract") else "")
-        out[name] = one(G, method, k, kw)
-    for name in ("louvain_k8", "louvain_k8_textbook", "louvain_k1", "leiden_k64", "leiden_k8", "lpa_k8"):
-        vs(out, name, name.split("_")[0] + "_k0")
-    for gname, make in (("sbm10k", lambda: gen.sbm_10k(1)), ("grid1024", lambda: gen.grid(1024, 1024, 0.02, 16, 1))):
+    def compare(r):
+        for name, v in r.items():
+            ex = r.get(name.split("_")[0] + "_k0")
+            if ex is None or name.endswith("_k0"):
+                continue
+            v["q_vs_exact"] = v["q"] / ex["q"] if ex["q"] else None
+            v["time_vs_exact"] = v["ms"] / ex["ms"]
+            v["scratch_vs_exact"] = v["scratch_bytes"] / max(ex["scratch_bytes"], 1)
+
+    runs = [(m, k, {}) for m in ("louvain", "leiden", "lpa") for k in (0, 4, 8, 16)]
+    runs += [("louvain", 1, {}), ("louvain", 8, {"subtract": 2}), ("leiden", 32, {}), ("leiden", 64, {}),
+             ("lpa", 8, {"one_scan": True})]
+    graphs = [(f"rmat22_seed{sd}", lambda sd=sd: gen.rmat(22, 16, wmax=16, seed=sd)) for sd in seeds]
+    if permuted:
+        graphs.append(("rmat22_seed1_permuted", lambda: gen.rmat(22, 16, wmax=16, seed=1, permute=True)))
+    out = {"graph": "R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), w in [1,16]"}
+    for gname, make in graphs:
         Gx = cd.Graph.to_device(make())
-        r = {f"louvain_k{k}": one(Gx, "louvain", k, {}) for k in (8, 0)}
-        r["louvain_k8_textbook"] = one(Gx, "louvain", 8, {"subtract": 2})
-        r.update({f"leiden_k{k}": one(Gx, "leiden", k, {}) for k in (64, 0)})
-        vs(r, "louvain_k8", "louvain_k0")
-        vs(r, "louvain_k8_textbook", "louvain_k0")
-        vs(r, "leiden_k64", "leiden_k0")
+        cd.cd_louvain(Gx, cd.make_params(k=8))  # warm-up
+        r = {name_of(m, k, kw): one(Gx, m, k, kw) for m, k, kw in runs}
+        compare(r)
         out[gname] = r
+        del Gx
+    # mean over the seeds of each run's ratios
+    keys = [f"rmat22_seed{sd}" for sd in seeds]
+    summary = {}
+    for name in out[keys[0]]:
+        if name.endswith("_k0"):
+            continue
+        qs = [out[kk][name].get("q_vs_exact") for kk in keys]
+        ts = [out[kk][name].get("time_vs_exact") for kk in keys]
+        if all(x is not None for x in qs):
+            summary[name] = {"q_vs_exact_mean": float(np.mean(qs)), "time_vs_exact_mean": float(np.mean(ts))}
+    out["mean_over_seeds"] = summary
+    if small:
+        for gname, make in (("sbm10k", lambda: gen.sbm_10k(1)),
+                            ("grid1024", lambda: gen.grid(1024, 1024, 0.02, 16, 1))):
+            Gx = cd.Graph.to_device(make())
+            r = {name_of(m, k, kw): one(Gx, m, k, kw)
+                 for m, k, kw in (("louvain", 8, {}), ("louvain", 0, {}), ("louvain", 8, {"subtract": 2}),
+                                  ("leiden", 64, {}), ("leiden", 0, {}))}
+            compare(r)
+            out[gname] = r
     return out
 
 
@@ -418,35 +474,109 @@ def run_reference(args, g, world):
             rates.append(r)
     v = float(np.mean(rates)) / 1e9
     line = {
-        "impl": "reference", "metric": "local-move GTEPS (Louvain, MG k=8 sweep)", "value": v, "unit": "GTEPS",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": g.nnz / (v * 1e9) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "nnz": g.nnz, "k": args.k,
-                   "mode": "louvain", "labels": "singletons"},
+        "config": workload_config(args, g, world),
         "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def time_sweeps(cd, torch, G, lab, k: int, steps: int, stream):
+    """`steps` cd_sweep calls from `lab`, timed with CUDA events on the
+    launching stream; returns (ms per step, sweep-kernel ms per launch, library
+    kernels launched, candidates evaluated per sweep, movers)."""
+    params = cd.make_params(k=k, stream=stream.cuda_stream, timing=True)
+    out = torch.empty_like(lab)
+    kern_ms, kern_launches, launches, cands, moved = 0.0, 0, 0, 0, 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        _, moved, _ = cd.cd_sweep(G, params, cd.MODE_LOUVAIN, lab, labels_out=out)
+        st = cd.cd_last_stats()
+        kern_ms += st.sweep_kernel_ms
+        kern_launches += st.sweep_kernel_launches
+        launches += st.kernel_launches  # every kernel of the library the step launched
+        cands += st.candidates
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return (ev0.elapsed_time(ev1) / steps, kern_ms / max(kern_launches, 1), launches, cands / max(steps, 1),
+            moved)
+
+
+def end_to_end(cd, torch, g, k: int, steps: int, out_dev):
+    """The same step through the C ABI with pinned host buffers (the call
+    copies the CSR and labels in and the labels out); returns the e2e object.
+    Beside it, the time of the bare host-to-device copies of the same bytes
+    (the bound of this path)."""
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    ho, hc, hw = pin(g.offsets), pin(g.cols), pin(g.w.view(np.int32))
+    hl = pin(np.arange(g.n, dtype=np.uint32).view(np.int32))
+    hout = pin(np.empty(g.n, dtype=np.int32))
+    Gh = cd.Graph(g.n, ho.numpy(), hc.numpy(), hw.numpy().view(np.uint32))
+    lab_h, out_h = hl.numpy().view(np.uint32), hout.numpy().view(np.uint32)
+    ph = cd.make_params(k=k, stream=torch.cuda.current_stream().cuda_stream)
+    for _ in range(3):  # warm-up: the first calls grow the device memory pool
+        cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
+    torch.cuda.synchronize()
+    per, phases = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
+        per.append((time.perf_counter() - t0) * 1e3)
+        phases.append([round(x, 2) for x in cd.cd_last_stats().phase_ms])
+    # bare copies of the same bytes (three pinned tensors and the labels)
+    dev = [torch.empty(x.shape, dtype=x.dtype, device="cuda") for x in (ho, hc, hw, hl)]
+    for _ in range(2):
+        for d, h in zip(dev, (ho, hc, hw, hl)):
+            d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for d, h in zip(dev, (ho, hc, hw, hl)):
+        d.copy_(h, non_blocking=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    copy_ms = ev0.elapsed_time(ev1)
+    del dev
+    h2d = g.offsets.nbytes + g.cols.nbytes + g.w.nbytes + lab_h.nbytes
+    ms = float(np.mean(per))
+    return {"value": g.nnz / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_h.nbytes),
+            "ms_per_step": [round(x, 3) for x in per], "copy_bound_ms": copy_ms,
+            "phase_ms_per_step": phases,
+            "phases": "host clock at the end of: staging, host-input checks, degrees/buckets/totals, the call",
+            "vs_copy_bound": ms / copy_ms,
+            "note": "cd_sweep with pinned host CSR and labels: host-to-device copies, the sweep and the "
+                    "device-to-host labels inside each timed call; copy_bound_ms = bare pinned copies of "
+                    "the same input bytes",
+            "matches_device_run": bool(np.array_equal(out_h, out_dev.cpu().numpy().view(np.uint32)))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="rmat25", choices=list(WORKLOADS))
     ap.add_argument("--k", type=int, default=8)
+    ap.add_argument("--mid-steps", type=int, default=10,
+                    help="timed sweeps from the communities of the first Louvain pass (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-side", type=int, default=4096,
                     help="side of the rewired grid for the learned-skip comparison (0 = skip it)")
-    ap.add_argument("--learned-rmat", type=int, default=0,
+    ap.add_argument("--learned-rmat", type=int, default=24,
                     help="also compare the learned skip on an R-MAT graph of this scale (0 = no)")
     ap.add_argument("--variants", type=int, default=1,
                     help="1 = also run Louvain/Leiden/LPA with their sketch sizes against the exact hashtable")
+    ap.add_argument("--variant-seeds", type=int, default=3)
     ap.add_argument("--warm-seconds", type=float, default=1.0,
                     help="after the warm-up steps, keep stepping (untimed) for this long")
     ap.add_argument("--batch-count", type=int, default=512,
@@ -495,60 +625,46 @@ def main():
     while time.perf_counter() - t_w < args.warm_seconds:
         step()
     torch.cuda.synchronize()
-    kern_ms, kern_launches, all_launches = 0.0, 0, 0
     with ClockSampler(local) as clk:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        moved = 0
-        for _ in range(args.steps):
-            _, moved, _ = step()
-            st = cd.cd_last_stats()
-            kern_ms += st.sweep_kernel_ms
-            kern_launches += st.sweep_kernel_launches
-            all_launches += st.kernel_launches  # every kernel of the library the step launched
-        ev1.record(stream)
+        ms_step, kern_avg_ms, all_launches, cands, moved = time_sweeps(cd, torch, G, lab, args.k, args.steps,
+                                                                       stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, f"cuda:{local}")
+    ms = max_over_ranks(ms_step * args.steps, dist, f"cuda:{local}")
     all_launches = sum_over_ranks(all_launches, dist, f"cuda:{local}")  # every rank's kernels
     ms_step = ms / args.steps
     gteps = g.nnz * args.steps * world / (ms * 1e-3) / 1e9
     scratch = cd.cd_last_stats().scratch_bytes
+    step(); torch.cuda.synchronize()  # noqa: E702  (out = the singleton sweep, for the e2e check)
 
-    # end to end through the C ABI with pinned host buffers (copies inside the call)
-    e2e = None
-    if args.e2e_steps > 0:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-        Gh = cd.Graph(g.n, pin(g.offsets), pin(g.cols), pin(g.w))
-        lab_h = pin(np.arange(g.n, dtype=np.uint32))
-        out_h = pin(np.empty(g.n, dtype=np.uint32))
-        ph = cd.make_params(k=args.k, stream=stream.cuda_stream)
-        cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
-        dt = time.perf_counter() - t0
-        h2d = g.offsets.nbytes + g.cols.nbytes + g.w.nbytes + lab_h.nbytes
-        e2e = {"value": g.nnz * args.e2e_steps * world / dt / 1e9, "unit": "GTEPS",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_h.nbytes),
-               "note": "cd_sweep with host CSR/labels; host->device copy, sweep, device->host labels per step"}
-        ok = np.array_equal(out_h, out.cpu().numpy().view(np.uint32))
-        e2e["matches_device_run"] = bool(ok)
-
-    ab = algorithmic_bytes(g, args.k)
-    kern_avg_ms = kern_ms / max(kern_launches, 1)
     peak, peak_kind = measured_peak_hbm()
+    ab = algorithmic_bytes(g, args.k, cands)
     achieved = ab["bytes"] / (kern_avg_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, args.k)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_sweep_mg", "kernel_ms": kern_avg_ms,
-                "algorithmic_bytes": ab["bytes"], "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+                "algorithmic_bytes": ab["bytes"], "algorithmic": ab,
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)"}
+
+    # the same sweep from the communities of the first Louvain pass
+    mid = None
+    if args.mid_steps > 0:
+        lab_mid, q_mid = cd.cd_louvain(G, cd.make_params(k=args.k, max_passes=1))
+        time_sweeps(cd, torch, G, lab_mid, args.k, 2, stream)
+        m_ms, m_kern, _, m_cands, m_moved = time_sweeps(cd, torch, G, lab_mid, args.k, args.mid_steps, stream)
+        mab = algorithmic_bytes(g, args.k, m_cands)
+        mid = {"labels": "communities after the first Louvain pass (k=8)", "q_of_labels": q_mid,
+               "ms_per_step": m_ms, "gteps": g.nnz / (m_ms * 1e-3) / 1e9, "kernel_ms": m_kern,
+               "kernel_gteps": g.nnz / (m_kern * 1e-3) / 1e9, "moved": m_moved,
+               "candidates_per_sweep": m_cands, "algorithmic_bytes": mab["bytes"],
+               "roofline_frac": mab["bytes"] / (m_kern * 1e-3) / 1e9 / peak}
+        del lab_mid
+
+    e2e = end_to_end(cd, torch, g, args.k, args.e2e_steps, out) if args.e2e_steps > 0 else None
 
     learned = None
     if args.learned_side > 0 or args.learned_rmat > 0:
@@ -556,7 +672,11 @@ def main():
     batched = None
     if args.batch_count > 0:
         batched = batched_vs_plain(cd, torch, args.batch_count, dist, rank, world)
-    variants = variants_vs_exact(cd, torch, G) if args.variants else None
+    variants = None
+    if args.variants:
+        del G
+        torch.cuda.empty_cache()
+        variants = variants_vs_exact(cd, torch, seeds=tuple(range(1, args.variant_seeds + 1)))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -566,17 +686,15 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "local-move GTEPS (Louvain, MG k=8 sweep)", "value": gteps, "unit": "GTEPS",
+            "metric": METRIC, "value": gteps, "unit": "GTEPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]["desc"], "n": g.n, "nnz": g.nnz, "k": args.k,
-                       "mode": "louvain", "labels": "singletons", "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"replicas{world}", "scratch_bytes": scratch, "moved": moved,
-                       "gen_seconds": round(t_gen, 2)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "learned_vs_plain": learned,
-            "batched_vs_plain": batched,
-            "variants_vs_exact": variants,
+            "config": workload_config(args, g, world),
+            "run": {"scratch_bytes": scratch, "moved": moved, "gen_seconds": round(t_gen, 2),
+                    "candidates_per_sweep": cands},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mid_run": mid,
+            "learned_vs_plain": learned, "batched_vs_plain": batched, "variants_vs_exact": variants,
             "gpu_launches": all_launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -27,6 +27,11 @@
  *   modularity) synchronise the stream before returning.
  * Scratch: device scratch is allocated with cudaMallocAsync on the stream and
  *   freed before the call returns; its peak size is in cd_last_stats().
+ *   Fault injection (for tests of callers' error paths): when the
+ *   environment variable CD_FAIL_ALLOC holds n >= 1, the n-th scratch
+ *   allocation of every call fails with CD_ENOMEM on the host, before the
+ *   device is asked for it; what the call took before is released as on any
+ *   error.
  * Errors: every entry point returns CD_OK (0) or a negative code; it never
  *   aborts or traps.  cd_strerror() names the code.  After CD_ECUDA the
  *   CUDA error string is in cd_last_stats()->cuda_error.
@@ -126,9 +131,11 @@ typedef struct cd_params {
     int32_t colors;       /* drivers: each sweep is `colors` sub-sweeps, sub-sweep p deciding
                              the vertices i with lowbias32(i) mod colors = p from the state
                              left by the previous sub-sweeps (1 = fully synchronous sweeps,
-                             0 = default 8, at most 16); cd_sweep uses it in refine mode */
-    int32_t sub_color;    /* cd_sweep, refine mode: the colour class deciding in this sweep
-                             (pass the vertices of that class as `active`) */
+                             0 = default 8, at most 16).  cd_sweep: the classes of a
+                             sub-sweep (refine mode: 0 = 8; Louvain mode: 0 = 1, one class) */
+    int32_t sub_color;    /* cd_sweep: the colour class deciding in this sweep (pass the
+                             vertices of that class as `active`); the rules that guard
+                             against simultaneous moves read it (see cd_sweep) */
     int32_t one_scan;     /* LPA only (cd_sweep mode LPA, cd_lpa): the "1-scan" variant of
                              Section 4.3, deciding on the sketch values without the second
                              scan (needs k > 0) */
@@ -166,6 +173,14 @@ typedef struct cd_stats {
     char cuda_error[128];
     int64_t kernel_launches; /* kernels of this library launched by the last call (a CUDA-graph
                                 replay counts the kernels recorded in the graph) */
+    int64_t candidates;      /* MG sweeps (all sweeps): candidate communities evaluated by the
+                                vertices that decided (the live sketch slots other than d); each
+                                costs one gather of Sigma_c and of |c| */
+    double phase_ms[4];      /* cd_sweep, host wall clock from the call's start to the end of:
+                                [0] staging (device allocations, host inputs' copies enqueued),
+                                [1] the O(n) checks of host inputs, [2] degrees, buckets and
+                                totals (waits for offsets, labels and weights to arrive), [3]
+                                the call (sweep, labels copied out, statistics read) */
 } cd_stats;
 
 /* Modularity parts (Eq. 1): Q = (two_m * sigma_in - sum_Sigma2) / two_m^2
@@ -198,7 +213,10 @@ int cd_default_schedule(int k, cd_schedule* out);
  *   bound[j] == bound[i]);
  *   Louvain/refine: gain(c) = 2m (K_{i->c} - K_{i->d}) - K_i (K_i + Sigma_c - Sigma_d)
  *   (Eq. 2 times 2m^2, exact 128-bit integers); a vertex whose community is
- *   a singleton may not join another singleton community with a larger id;
+ *   a singleton may not join another singleton community with a larger id
+ *   whose id is in the deciding colour class (lowbias32(c) mod colors =
+ *   sub_color; with one class, every such community: no two singletons
+ *   swap);
  *   the largest gain wins, ties to the smaller id; the vertex moves iff the
  *   gain is positive.  Refine additionally moves only vertices whose
  *   community is a singleton.

@@ -444,7 +444,9 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
     """Local-moving phase from singletons, each sweep made of `colors`
     sub-sweeps: sub-sweep p decides the vertices of colour class p, all at
     once, from the state left by the previous sub-sweeps (colors=1: fully
-    synchronous sweeps).  Stops when nobody moves in a sweep, the sweep's
+    synchronous sweeps); Louvain's singleton rule bars only singleton targets
+    whose id falls in the deciding class (see or_sweep).  Stops when nobody
+    moves in a sweep, the sweep's
     summed delta-Q is <= tol (Louvain) or at most tol * n labels changed
     (LPA), or after max_sweeps.  Returns (labels, sweeps)."""
     n = g.n
@@ -456,10 +458,11 @@ def local_move_sync(g, mode, k, uncond, tol, max_sweeps, sched, threads=1, color
     sweeps = 0
     while sweeps < max_sweeps:
         moved, gsum = 0, 0
-        for act in masks:
+        for p, act in enumerate(masks):
             Sig, size = community_totals(n, labels, K)
             out, gains = sweep(g, labels, mode, k, uncond, sched, active=act if colors > 1 else None,
-                               threads=threads, state=(K, Sig, size, two_m), one_scan=one_scan)
+                               threads=threads, state=(K, Sig, size, two_m), one_scan=one_scan,
+                               colors=max(colors, 1), sub_color=p)
             moved += int(np.count_nonzero(out != labels))
             gsum += gain_total(gains)
             labels = out

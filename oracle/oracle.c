@@ -253,8 +253,11 @@ static i128 dq_gain(uint64_t two_m, uint64_t Kic, uint64_t Kid, uint64_t Ki, uin
  * The current community d is never a candidate; K_{i->d} is always exact.
  *
  * Louvain (and refine): gain as above; a singleton vertex may not join another
- * singleton community with a larger id (stops pairwise swaps in a synchronous
- * sweep); best gain wins, ties to the smaller id; moves iff gain > 0.
+ * singleton community with a larger id whose id has colour `sub_color` among
+ * `colors` (that is, whose vertex decides in the same sub-sweep: this stops
+ * pairwise swaps of simultaneous moves; colors = 1, a fully synchronous
+ * sweep, bars every such target); best gain wins, ties to the smaller id;
+ * moves iff gain > 0.
  * LPA: largest K_{i->c} wins, ties to the smaller id; moves iff it exceeds
  * K_{i->d}.
  * Refine (Leiden, Section 3.4): both scans are restricted to neighbours with
@@ -337,7 +340,9 @@ void or_sweep(int64_t n, const int64_t* off, const int32_t* cols, const uint32_t
                     best = c; best_k = Kic; have = 1;
                 }
             } else {
-                if (mode == MODE_LOUVAIN && size[d] == 1 && size[c] == 1 && c > d) continue;
+                if (mode == MODE_LOUVAIN && size[d] == 1 && size[c] == 1 && c > d &&
+                    (int)color_of(c, colors) == sub_color)
+                    continue;
                 if (mode == MODE_REFINE && size[c] == 1 && (int)color_of(c, colors) == sub_color) continue;
                 i128 g = dq_gain(two_m, Kic, Kid, K[i], Sigma[c], Sigma[d]);
                 if (g > 0 && (g > best_gain || (g == best_gain && c < best))) {
@@ -366,6 +371,52 @@ void or_row_sketch(int64_t i, const int64_t* off, const int32_t* cols, const uin
                    uint64_t* vals) {
     or_sched sched = {nbuckets, deg_max, lanes, vec};
     row_sketch(i, off, cols, w, labels, bound, k, uncond, &sched, keys, vals);
+}
+
+/* Linking weights of row i to every neighbouring community (self-loops
+ * excluded): the row's (C_j, w_ij) pairs sorted by community and summed per
+ * community.  Writes the distinct communities other than d to cand[] with
+ * their weights in wsum[] (ascending id), returns their number, and stores
+ * K_{i->d} in *kid.  The same sums as link_weight() for each community, in
+ * O(deg log deg) instead of O(deg^2): used by the sequential exact sweep on
+ * rows with hundreds of thousands of entries. */
+typedef struct { uint32_t c; uint32_t w; } or_pair;
+
+static int cmp_pair(const void* a, const void* b) {
+    const uint32_t x = ((const or_pair*)a)->c, y = ((const or_pair*)b)->c;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int64_t row_community_weights(int64_t i, uint32_t d, const int64_t* off, const int32_t* cols,
+                                     const uint32_t* w, const uint32_t* labels, uint32_t* cand,
+                                     uint64_t* wsum, uint64_t* kid) {
+    int64_t deg = off[i + 1] - off[i];
+    or_pair* pr = (or_pair*)malloc(sizeof(or_pair) * (size_t)(deg > 0 ? deg : 1));
+    int64_t np = 0;
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        if (cols[e] == i) continue;
+        pr[np].c = labels[cols[e]];
+        pr[np].w = w[e];
+        ++np;
+    }
+    qsort(pr, (size_t)np, sizeof(or_pair), cmp_pair);
+    int64_t ncand = 0;
+    *kid = 0;
+    for (int64_t a = 0; a < np;) {
+        uint64_t s = 0;
+        int64_t b = a;
+        while (b < np && pr[b].c == pr[a].c) s += pr[b++].w;
+        if (pr[a].c == d) {
+            *kid = s;
+        } else {
+            cand[ncand] = pr[a].c;
+            wsum[ncand] = s;
+            ++ncand;
+        }
+        a = b;
+    }
+    free(pr);
+    return ncand;
 }
 
 /* ---------------------------------------------------------------------------
@@ -401,30 +452,26 @@ int or_local_move_seq(int64_t n, const int64_t* off, const int32_t* cols, const 
             uint32_t d = labels[i];
             int64_t deg = off[i + 1] - off[i];
             uint32_t* cand = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(deg > kk ? deg : kk));
+            uint64_t* wsum = NULL;
+            uint64_t Kid = 0;
             int64_t ncand = 0;
-            if (k > 0) {
+            if (k == 0) {
+                /* exact: every neighbouring community, weights by sorting */
+                wsum = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(deg > 0 ? deg : 1));
+                ncand = row_community_weights(i, d, off, cols, w, labels, cand, wsum, &Kid);
+            } else if (k > 0) {
                 row_sketch(i, off, cols, w, labels, NULL, k, uncond, &sched, keys, vals);
                 for (int p = 0; p < k; ++p)
                     if (vals[p] > 0 && keys[p] != d) cand[ncand++] = keys[p];
-            } else {
-                for (int64_t e = off[i]; e < off[i + 1]; ++e) {
-                    if (cols[e] == i) continue;
-                    uint32_t c = labels[cols[e]];
-                    if (c == d) continue;
-                    int seen = 0;
-                    for (int64_t q = 0; q < ncand; ++q)
-                        if (cand[q] == c) { seen = 1; break; }
-                    if (!seen) cand[ncand++] = c;
-                }
             }
-            uint64_t Kid = link_weight(i, d, off, cols, w, labels, NULL);
+            if (k > 0) Kid = link_weight(i, d, off, cols, w, labels, NULL);
             uint32_t best = d;
             i128 best_gain = 0;
             uint64_t best_k = Kid;
             int have = 0;
             for (int64_t q = 0; q < ncand; ++q) {
                 uint32_t c = cand[q];
-                uint64_t Kic = link_weight(i, c, off, cols, w, labels, NULL);
+                uint64_t Kic = k == 0 ? wsum[q] : link_weight(i, c, off, cols, w, labels, NULL);
                 if (mode == MODE_LPA) {
                     if (Kic > Kid && (Kic > best_k || (Kic == best_k && c < best))) {
                         best = c; best_k = Kic; have = 1;
@@ -437,6 +484,7 @@ int or_local_move_seq(int64_t n, const int64_t* off, const int32_t* cols, const 
                 }
             }
             free(cand);
+            free(wsum);
             if (have) {
                 Sig[d] -= K[i]; size[d] -= 1;
                 Sig[best] += K[i]; size[best] += 1;

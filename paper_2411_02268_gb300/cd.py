@@ -87,7 +87,8 @@ class Stats(ctypes.Structure):
                 ("sweep_kernel_ms", ctypes.c_double), ("sweep_kernel_launches", ctypes.c_int64),
                 ("modularity", ctypes.c_double), ("entries_scanned", ctypes.c_int64),
                 ("full_sweeps", ctypes.c_int64), ("cuda_error", ctypes.c_char * 128),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("phase_ms", ctypes.c_double * 4)]
 
 
 TUNE_MAX_K = 8

@@ -3,9 +3,11 @@
 // staging.  Every entry point returns a status code and never aborts.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -65,20 +67,36 @@ void keep_pool_memory() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
 }
 
+// Fault injection for tests: with CD_FAIL_ALLOC=n (n >= 1) in the
+// environment, the n-th scratch allocation of every call fails as out of
+// memory on the host, before the device is asked for anything.
+int64_t injected_alloc_failure() {
+    const char* e = std::getenv("CD_FAIL_ALLOC");
+    if (!e || !*e) return 0;
+    char* end = nullptr;
+    const long long v = std::strtoll(e, &end, 10);
+    return (end && *end == 0 && v > 0) ? (int64_t)v : 0;
+}
+
 // Stream-ordered device scratch of one call; everything is released (in stream
 // order) when the object goes out of scope.
 struct Scratch {
     cudaStream_t s;
     std::vector<void*> ptrs;
     int64_t bytes = 0;
-    explicit Scratch(cudaStream_t st) : s(st) { keep_pool_memory(); }
+    int64_t fail_at = 0, count = 0;
+    explicit Scratch(cudaStream_t st) : s(st), fail_at(injected_alloc_failure()) { keep_pool_memory(); }
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, s);
         if (bytes > g_stats.scratch_bytes) g_stats.scratch_bytes = bytes;
     }
     template <typename T>
-    int get(T** p, int64_t count) {
-        size_t nb = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    int get(T** p, int64_t count_) {
+        if (fail_at > 0 && ++count == fail_at) {
+            std::snprintf(g_stats.cuda_error, sizeof(g_stats.cuda_error), "injected allocation failure");
+            return CD_ENOMEM;
+        }
+        size_t nb = sizeof(T) * (size_t)(count_ > 0 ? count_ : 1);
         nb = (nb + 255) & ~(size_t)255;
         void* q = nullptr;
         cudaError_t e = cudaMallocAsync(&q, nb, s);
@@ -805,7 +823,9 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
                                     cudaMemcpyDeviceToDevice, st));
             Level Lc = L;
             Lc.bt = L.table_for(c);
-            SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract);
+            SweepArgs a = make_args(Lc, la, lb, use_mask ? active : nullptr, nullptr, dglob, mode, p->subtract,
+                                    colors, c);
+            a.cid = L.cid;
             a.one_scan = p->one_scan;
             a.attach = attach;
             a.out_all = 0;  // k_commit reads the movers' entries of lb only
@@ -904,6 +924,7 @@ int local_move(Level& L, const cd_params* p, int mode, double tol, const cd_sche
         g_stats.gain_lo = hg.g.gain_lo;
         g_stats.gain_hi = hg.g.gain_hi;
         g_stats.entries_scanned += (int64_t)hg.g.scanned;
+        g_stats.candidates += (int64_t)hg.g.cands;
         if (!use_mask) g_stats.full_sweeps += 1;
         if (B) {
             if (hg.g.count == 0) break;  // every graph has stopped
@@ -1136,6 +1157,10 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     cd_schedule sched;
     if (p->sched) sched = *p->sched; else default_schedule(p->k, &sched);
     const bool host = g->memory == CD_MEM_HOST;
+    const auto t_start = std::chrono::steady_clock::now();
+    auto since_ms = [&](std::chrono::steady_clock::time_point t) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+    };
     HostCheck hc;
     hc.start(g, labels_in);
     Scratch sc(s);
@@ -1149,7 +1174,6 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     auto stage = [&]() -> int {
         // allocations are ordered on s; the copies run on the side stream
         int64_t *off; int32_t* cols; uint32_t* w; uint32_t* li;
-        CD_TRY(side.init());
         CD_TRY(sc.get(&off, g->n + 1));
         CD_TRY(sc.get(&li, g->n));
         CD_TRY(sc.get(&w, g->nnz));
@@ -1159,6 +1183,7 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         uint32_t* db = nullptr;
         if (active) CD_TRY(sc.get(&da, g->n));
         if (bound) CD_TRY(sc.get(&db, g->n));
+        CD_TRY(side.init());
         CD_CUDA(cudaEventRecord(side.ev[0], s));
         CD_CUDA(cudaStreamWaitEvent(side.cs, side.ev[0], 0));  // the allocations precede the copies
         CD_CUDA(cudaMemcpyAsync(off, g->offsets, sizeof(int64_t) * (g->n + 1), cudaMemcpyHostToDevice, side.cs));
@@ -1182,7 +1207,9 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     };
     if (host) {
         const int st = stage();
+        g_stats.phase_ms[0] = since_ms(t_start);
         CD_TRY(hc.join());  // bad host inputs are reported as such, staged or not
+        g_stats.phase_ms[1] = since_ms(t_start);
         CD_TRY(st);
     } else {
         L.off = g->offsets; L.cols = g->cols; L.w = g->weights;
@@ -1195,8 +1222,12 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
         return CD_OK;
     }
     CD_TRY(prepare_level(L, lin, lout, p->k, sched, 1, sc, dglob, s, false, host ? side.ev[1] : nullptr));
+    g_stats.phase_ms[2] = since_ms(t_start);
     if (host) CD_CUDA(cudaStreamWaitEvent(s, side.ev[2], 0));  // the columns before the sweep
-    SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, resolve_colors(p), p->sub_color);
+    // refine: the driver's colour classes (0 = 8); Louvain: the singleton
+    // rule's classes (0 = one class, every vertex decides together)
+    const int ncol = mode == CD_MODE_REFINE ? resolve_colors(p) : (p->colors == 0 ? 1 : p->colors);
+    SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, ncol, p->sub_color);
     a.one_scan = p->one_scan;
     Timer tm;
     CD_TRY(tm.init(p->timing != 0));
@@ -1215,11 +1246,13 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     g_stats.sweeps = 1;
     g_stats.full_sweeps = active ? 0 : 1;
     g_stats.entries_scanned = (int64_t)hg.g.scanned;
+    g_stats.candidates = (int64_t)hg.g.cands;
     g_stats.moved = (int64_t)hg.g.moved;
     g_stats.gain_lo = hg.g.gain_lo;
     g_stats.gain_hi = hg.g.gain_hi;
     if (moved_out) *moved_out = (int64_t)hg.g.moved;
     if (gain_out) { gain_out[0] = hg.g.gain_lo; gain_out[1] = hg.g.gain_hi; }
+    g_stats.phase_ms[3] = since_ms(t_start);
     return CD_OK;
 }
 

@@ -28,6 +28,7 @@ struct Globals {
     unsigned long long gain_lo;  // 128-bit sum of movers' gains
     unsigned long long gain_hi;
     unsigned long long scanned;  // CSR entries of the vertices that decided
+    unsigned long long cands;    // MG sweeps: candidates evaluated by the vertices that decided
     unsigned long long sigma_in; // modularity: sum_c sigma_c
     unsigned long long sq_lo;    // modularity: sum_c Sigma_c^2
     unsigned long long sq_hi;
@@ -85,8 +86,9 @@ struct SweepArgs {
     int one_scan;             // LPA: decide on sketch values, no second scan
     int out_all;              // 1: labels_out for every listed vertex; 0: only for the deciding ones
                               // (the drivers read labels_out of movers only)
-    int colors;               // refine: colour classes of the driver
-    int sub_color;            // refine: colour class deciding in this sub-sweep
+    int colors;               // colour classes of the driver (1: a fully synchronous sweep)
+    int sub_color;            // colour class deciding in this sub-sweep
+    const uint32_t* cid;      // colour id of every vertex (its id inside its graph); null = the vertex id
     BucketTable bt;
 };
 
@@ -136,18 +138,25 @@ __device__ __forceinline__ void graph_stats(const SweepArgs& a, uint32_t i, u128
     if (hi + carry) atomicAdd(&a.g_gain_hi[g], hi + carry);
 }
 
+// Whether the singleton community c may be left by its vertex in the
+// deciding sub-sweep: its id has the sub-sweep's colour.
+__device__ __forceinline__ bool deciding_colour(const SweepArgs& a, uint32_t c) {
+    return (int)color_of(a.cid ? a.cid[c] : c, a.colors) == a.sub_color;
+}
 // Refine mode (Leiden): a singleton community whose vertex has the colour of
 // the deciding sub-sweep is not a candidate (its only member may leave in the
-// same sub-sweep).  Louvain: a singleton may not join a larger-id singleton.
+// same sub-sweep).  Louvain: a singleton may not join a larger-id singleton
+// that decides in the same sub-sweep (no pairwise swaps of simultaneous
+// moves; with one colour class that is every singleton).
 __device__ __forceinline__ bool barred(const SweepArgs& a, uint32_t c, uint32_t d, bool d_single) {
-    if (a.mode == CD_MODE_REFINE) return a.size[c] == 1 && (int)color_of(c, a.colors) == a.sub_color;
-    return d_single && c > d && a.size[c] == 1;
+    if (a.mode == CD_MODE_REFINE) return a.size[c] == 1 && deciding_colour(a, c);
+    return d_single && c > d && a.size[c] == 1 && deciding_colour(a, c);
 }
 // barred() with |c| already loaded.
 __device__ __forceinline__ bool barred_n(const SweepArgs& a, uint32_t c, uint32_t d, bool d_single,
                                          uint32_t size_c) {
-    if (a.mode == CD_MODE_REFINE) return size_c == 1 && (int)color_of(c, a.colors) == a.sub_color;
-    return d_single && c > d && size_c == 1;
+    if (a.mode == CD_MODE_REFINE) return size_c == 1 && deciding_colour(a, c);
+    return d_single && c > d && size_c == 1 && deciding_colour(a, c);
 }
 
 // Lanes per stream of the MG sweep kernel for sketch size k (the slot form

@@ -207,15 +207,16 @@ __device__ __forceinline__ Chunk load_chunk(const SweepArgs& a, int64_t ch) {
 template <typename F>
 __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, int64_t c1, int step,
                                             int64_t start, int64_t end, uint32_t i, uint32_t bi, F&& f) {
+    const uint32_t len = (uint32_t)(end - start);
     for (int64_t ch = first; ch < c1; ch += step) {
         Chunk cur = load_chunk(a, ch);
-        const int64_t e0 = ch * 4;
+        // entry offsets within the row, wrapping below 0 for entries before it
+        const uint32_t rel = (uint32_t)(ch * 4 - start);
         uint32_t labs[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int64_t e = e0 + u;
-            const bool in_row = e >= start && e < end;
+            const bool in_row = rel + (uint32_t)u < len;
             const bool in_range = (uint32_t)cur.c[u] < (uint32_t)a.n;
             if (in_row && !in_range) atomicOr(&a.glob->err, kErrBadCol);
             ok[u] = in_row && in_range && (uint32_t)cur.c[u] != i;
@@ -262,6 +263,7 @@ struct Outcome {
     u128 gain;
     uint32_t vertex;
     uint32_t scanned;  // entries of the row, when the vertex decided
+    uint32_t ncand;    // candidates it evaluated (each costs a Sigma_c and a size gather)
 };
 
 // Feeds the live slots of a partner sketch (keys pk, values pv) to s.
@@ -329,7 +331,7 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu
                                      : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    Outcome out{false, 0, 0, 0};
+    Outcome out{false, 0, 0, 0, 0};
     uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
@@ -442,6 +444,8 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         out.gain = g;
         out.vertex = i;
         out.scanned = (uint32_t)(end - start);
+#pragma unroll
+        for (int p = 0; p < K; ++p) out.ncand += cand[p] != kEmpty ? 1u : 0u;
     } else if (valid && !act && lane == 0 && a.out_all) {
         a.labels_out[i] = d;
     }
@@ -509,7 +513,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     const int bar = 1 + sb;
     const int wl = s >> 5;          // warp within sub-block
     const int lane = s & 31;
-    Outcome out{false, 0, 0, 0};
+    Outcome out{false, 0, 0, 0, 0};
     uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
@@ -599,6 +603,8 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
             out.gain = g;
             out.vertex = i;
             out.scanned = (uint32_t)(end - start);
+#pragma unroll
+            for (int p = 0; p < K; ++p) out.ncand += cand[p] != kEmpty ? 1u : 0u;
         } else if (valid && a.out_all) {
             a.labels_out[i] = d;
         }
@@ -611,7 +617,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
 // and the block's first slot in the mover list.
 struct EpiSmem {
     unsigned cnt;
-    unsigned long long lo, hi, scanned, base;
+    unsigned long long lo, hi, scanned, cands, base;
 };
 
 // Block-level statistics and mover list: warp sums go to shared memory and
@@ -620,9 +626,10 @@ struct EpiSmem {
 // call it.
 __device__ __forceinline__ void block_epilogue(const SweepArgs& a, const Outcome& o, EpiSmem& e) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) { e.cnt = 0; e.lo = 0; e.hi = 0; e.scanned = 0; }
+    if (threadIdx.x == 0) { e.cnt = 0; e.lo = 0; e.hi = 0; e.scanned = 0; e.cands = 0; }
     __syncthreads();
     const unsigned sc = __reduce_add_sync(0xffffffffu, o.scanned);
+    const unsigned nc = __reduce_add_sync(0xffffffffu, o.ncand);
     const unsigned mm = __ballot_sync(0xffffffffu, o.moved);
     unsigned woff = 0;
     if (mm) {
@@ -646,9 +653,11 @@ __device__ __forceinline__ void block_epilogue(const SweepArgs& a, const Outcome
         if (o.moved && a.gid) graph_stats(a, o.vertex, o.gain);
     }
     if (lane == 0 && sc) atomicAdd(&e.scanned, (unsigned long long)sc);
+    if (lane == 0 && nc) atomicAdd(&e.cands, (unsigned long long)nc);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (e.scanned) atomicAdd(&a.glob->scanned, e.scanned);
+        if (e.cands) atomicAdd(&a.glob->cands, e.cands);
         if (e.cnt) {
             e.base = atomicAdd(&a.glob->moved, (unsigned long long)e.cnt);
             unsigned long long old = atomicAdd(&a.glob->gain_lo, e.lo);

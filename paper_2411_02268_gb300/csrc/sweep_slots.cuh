@@ -248,7 +248,7 @@ __device__ __forceinline__ Outcome slot_body(const SweepArgs& a, int64_t vi, boo
     const int q = u % Q;                 // part of the sketch
     const int rowbase = threadIdx.x - u;
     SlotGroup<Q> g{q, (int)(threadIdx.x & 31) & ~(Q - 1)};
-    Outcome out{false, 0, 0, 0};
+    Outcome out{false, 0, 0, 0, 0};
     uint32_t i = 0, d = 0, bi = 0;
     int64_t start = 0, end = 0;
     bool act = valid;
@@ -366,6 +366,12 @@ __device__ __forceinline__ Outcome slot_body(const SweepArgs& a, int64_t vi, boo
         }
         row_sync<T>();
     }
+    // candidates of the row (each lane holds 8 of them), summed over the group
+    int nc = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) nc += cand[p] != kEmpty ? 1 : 0;
+#pragma unroll
+    for (int off = 1; off < Q; off <<= 1) nc += __shfl_xor_sync(kFullWarp, nc, off);
     uint32_t best;
     u128 gain;
     VT bw;
@@ -379,6 +385,7 @@ __device__ __forceinline__ Outcome slot_body(const SweepArgs& a, int64_t vi, boo
             out.gain = gain;
             out.vertex = i;
             out.scanned = (uint32_t)(end - start);
+            out.ncand = (uint32_t)nc;
         } else if (valid && a.out_all) {
             a.labels_out[i] = d;
         }

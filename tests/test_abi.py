@@ -48,7 +48,7 @@ int main(void) {
   printf("csr %zu %zu %zu\n", sizeof(cd_csr), offsetof(cd_csr, weights), offsetof(cd_csr, memory));
   printf("sched %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes));
   printf("params %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors), offsetof(cd_params, one_scan), offsetof(cd_params, capture));
-  printf("stats %zu %zu %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, entries_scanned), offsetof(cd_stats, cuda_error), offsetof(cd_stats, kernel_launches));
+  printf("stats %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, entries_scanned), offsetof(cd_stats, cuda_error), offsetof(cd_stats, kernel_launches), offsetof(cd_stats, candidates), offsetof(cd_stats, phase_ms));
   printf("mlp %zu %zu\n", sizeof(cd_mlp), offsetof(cd_mlp, b2));
   printf("parts %zu\n", sizeof(cd_modularity_parts));
   printf("tune %zu %zu %zu %zu\n", sizeof(cd_tune_report), offsetof(cd_tune_report, q_mean), offsetof(cd_tune_report, trials), offsetof(cd_tune_report, chosen));
@@ -62,7 +62,7 @@ int main(void) {
         f"csr {C.sizeof(cd.CSR)} {cd.CSR.weights.offset} {cd.CSR.memory.offset}",
         f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset}",
         f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset} {cd.Params.one_scan.offset} {cd.Params.capture.offset}",
-        f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.entries_scanned.offset} {cd.Stats.cuda_error.offset} {cd.Stats.kernel_launches.offset}",
+        f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.entries_scanned.offset} {cd.Stats.cuda_error.offset} {cd.Stats.kernel_launches.offset} {cd.Stats.candidates.offset} {cd.Stats.phase_ms.offset}",
         f"mlp {C.sizeof(cd.MLP)} {cd.MLP.b2.offset}",
         f"parts {C.sizeof(cd.ModularityParts)}",
         f"tune {C.sizeof(cd.TuneReport)} {cd.TuneReport.q_mean.offset} {cd.TuneReport.trials.offset} {cd.TuneReport.chosen.offset}",
@@ -131,3 +131,28 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(cdmod, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         cdmod.lib()
+
+
+def test_bench_schedule_literal_matches_library(cd):
+    """bench.py's oracle legs use a written-out copy of the default schedule
+    (so that they never load the CUDA library); it must be the library's."""
+    import bench
+    for k in (0, 1, 2, 4, 8, 16, 32, 64):
+        assert tuple(bench.default_schedule(k)) == tuple(cd.cd_default_schedule(k).as_lists()), k
+
+
+def test_injected_allocation_failure_without_gpu(cd, monkeypatch):
+    """CD_FAIL_ALLOC=1 fails the first scratch allocation of a call on the
+    host, before any device request: cd_sweep and cd_louvain on host graphs
+    return CD_ENOMEM (this runs without a GPU)."""
+    from paper_2411_02268_gb300 import gen
+    g = gen.sbm(200, 4, 0.2, 0.02, seed=1)
+    G = cd.Graph.host(g)
+    lab = np.arange(g.n, dtype=np.uint32)
+    monkeypatch.setenv("CD_FAIL_ALLOC", "1")
+    for fn in (lambda: cd.cd_sweep(G, cd.make_params(k=8), cd.MODE_LOUVAIN, lab),
+               lambda: cd.cd_louvain(G, cd.make_params(k=8))):
+        with pytest.raises(cd.CDError) as e:
+            fn()
+        assert e.value.code == cd.CD_ENOMEM
+        assert cd.cd_last_stats().cuda_error == b"injected allocation failure"

@@ -199,3 +199,25 @@ def test_louvain_leiden_with_mg_aggregation(env, gname):
     lab, q2 = cd.cd_leiden(G, cd.make_params(k=8, agg_k=8))
     ref = oracle.leiden_sync(g, k=8, sched=sched_of(cd, 8), threads=8, agg_k=8, agg_sched=sched_of(cd, 16))
     assert np.array_equal(lab.cpu().numpy().view(np.uint32), ref)
+
+
+@pytest.mark.parametrize("k", [8, 0])
+def test_rmat22_louvain_within_tolerance_of_sequential_golden(env, k):
+    """At the benchmark's scale-22 R-MAT size: cd_louvain (colour-class
+    sub-sweeps, concurrent moves inside a class) ends within 0.005 of the
+    modularity of the oracle's sequential Louvain, or above it.  The
+    reference value is stored in tests/golden/rmat22_seq_q.json, written by
+    tests/golden/make_seq_q.py from oracle/ alone (a sequential run takes
+    minutes on the host)."""
+    import json
+    import os
+    cd, torch = env
+    path = os.path.join(os.path.dirname(__file__), "golden", "rmat22_seq_q.json")
+    with open(path) as f:
+        t = json.load(f)
+    if f"k{k}" not in t:
+        pytest.skip(f"no sequential value for k={k} in {path}")
+    g = gen.rmat22(1)
+    assert (g.n, g.nnz, gen.checksum(g)) == (t["graph"]["n"], t["graph"]["nnz"], t["graph"]["checksum"])
+    _, q = cd.cd_louvain(cd.Graph.to_device(g), cd.make_params(k=k))
+    assert q >= t[f"k{k}"]["q"] - 0.005, (q, t[f"k{k}"]["q"])

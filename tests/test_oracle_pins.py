@@ -682,3 +682,38 @@ def test_adam_step_size_and_scale_invariance(seed):
         p, m1, m2 = mlp.adam_step(p, gt, m1, m2, t, 0.01, eps=0.0)
         q, n1, n2 = mlp.adam_step(q, 37.5 * gt, n1, n2, t, 0.01, eps=0.0)
         assert np.allclose(p, q, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("mode", [oracle.MODE_LOUVAIN, oracle.MODE_LPA])
+def test_sequential_exact_sweep_is_locally_optimal(seed, mode):
+    """The sequential exact local-moving phase (k = 0, run until a sweep moves
+    nobody) ends in a state where no single move helps: Louvain, every move
+    of a vertex to a neighbouring community leaves Q unchanged or lower (exact
+    rationals, Eq. 1); LPA, every vertex's label has the largest linking
+    weight among its neighbouring communities (or ties it).  The synchronous
+    exact sweep (a separately written candidate scan) then moves nobody."""
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(6, 30))
+    g = gen.random_graph(n, int(rng.integers(n, 4 * n)), 9, seed=700 + seed, self_loops=bool(seed % 2))
+    lab, _ = oracle.local_move_seq(g, np.arange(n, dtype=np.uint32), mode, 0, False, 0.0, 500)
+    # ... the phase stopped because a sweep moved nobody
+    again, _ = oracle.local_move_seq(g, lab, mode, 0, False, 0.0, 1)
+    assert np.array_equal(again, lab)
+    q0 = oracle.modularity_fraction(g, lab)
+    for i in range(n):
+        nb = {int(lab[int(j)]) for j in g.cols[g.offsets[i]:g.offsets[i + 1]] if int(j) != i}
+        link = {}
+        for e in range(g.offsets[i], g.offsets[i + 1]):
+            j = int(g.cols[e])
+            if j != i:
+                link[int(lab[j])] = link.get(int(lab[j]), 0) + int(g.w[e])
+        for c in nb - {int(lab[i])}:
+            if mode == oracle.MODE_LOUVAIN:
+                moved = lab.copy()
+                moved[i] = c
+                assert oracle.modularity_fraction(g, moved) <= q0
+            else:
+                assert link[c] <= link.get(int(lab[i]), 0)
+    out, _ = oracle.sweep(g, lab, mode, 0)
+    assert np.array_equal(out, lab)

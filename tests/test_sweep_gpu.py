@@ -428,3 +428,23 @@ def test_modularity_rejects_offsets_short_of_the_entries(env):
     # and the well-formed graph still gives the oracle's parts afterwards
     q, parts = cd.cd_modularity(cd.Graph.to_device(g), lab)
     assert parts == oracle.modularity_parts(g, np.arange(g.n, dtype=np.uint32))
+
+
+@pytest.mark.parametrize("k", [8, 16, 64])
+def test_candidate_count_matches_oracle(env, k):
+    """cd_stats.candidates (the benchmark's count of Sigma_c gathers) equals
+    the number of live sketch slots other than the vertex's own community,
+    summed over the vertices that decide, with the oracle's sketches."""
+    cd, torch = env
+    g = gen.rmat(11, 16, wmax=16, seed=7)
+    osched = oracle_sched(cd, cd.cd_default_schedule(k))
+    deg = g.degrees()
+    for _, lab in label_states(g, 5):
+        G = cd.Graph.to_device(g)
+        cd.cd_sweep(G, cd.make_params(k=k), cd.MODE_LOUVAIN, torch.from_numpy(lab.view(np.int32)).cuda())
+        got = cd.cd_last_stats().candidates
+        want = 0
+        for i in np.nonzero(deg)[0]:
+            keys, vals = oracle.row_sketch(g, int(i), lab, k, osched)
+            want += int(np.count_nonzero((vals > 0) & (keys != lab[i])))
+        assert got == want
