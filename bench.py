@@ -435,6 +435,28 @@ def batched_vs_plain(cd, torch, count: int, dist=None, rank: int = 0, world: int
     tp = max_over_ranks(time.perf_counter() - t, dist, device)
     for a, b in zip(labs, outs):
         same += bool(torch.equal(a, b))
+    # the autotuner's schedule and k for this batch, and the batched run with them
+    tuned = None
+    if dev:
+        t0 = time.perf_counter()
+        tsched, tk, rep = cd.cd_autotune(dev, p, ks=(4, 8, 16), q_tol=0.005)
+        t_tune = time.perf_counter() - t0
+        pt = cd.make_params(k=tk, schedule=tsched)
+        cd.cd_louvain_batched(dev[:16], pt)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t = time.perf_counter()
+        _, qt, _ = cd.cd_louvain_batched(dev, pt)
+        torch.cuda.synchronize()
+        tt = max_over_ranks(time.perf_counter() - t, dist, device)
+        deg, lanes, _ = tsched.as_lists()
+        tuned = {"k": tk, "deg_max": [int(x) for x in deg], "lanes": lanes,
+                 "blocks_per_sm": int(tsched.blocks_per_sm), "tune_seconds": round(t_tune, 2),
+                 "trials": int(rep.trials), "default_sweep_ms": rep.default_ms,
+                 "tuned_sweep_ms": [rep.sweep_ms[i] for i in range(3)],
+                 "run_ms_per_k": [rep.run_ms[i] for i in range(3)], "q_mean_per_k": [rep.q_mean[i] for i in range(3)],
+                 "batched_ms": tt * 1e3, "speedup_vs_plain": tp / tt, "q_mean": float(np.mean(qt))}
     qb, qp = np.asarray(qb), np.asarray(qp)
     if dist is not None:
         tt = torch.tensor([same, float(qb.sum()), float(qp.sum()), float(np.max(np.abs(qb - qp), initial=0.0)),
@@ -454,6 +476,7 @@ def batched_vs_plain(cd, torch, count: int, dist=None, rank: int = 0, world: int
         "graphs": count, "n_total": N, "nnz_total": M, "gen_seconds": round(t_gen, 1), "ranks": world,
         "sharding": "LPT on expected CSR entries" if world > 1 else "none",
         "batched": {"ms": tb * 1e3, "gteps": M / tb / 1e9, "q_mean": qbm, "union_rank0": union},
+        "autotuned_rank0": tuned,
         "plain_per_graph": {"ms": tp * 1e3, "gteps": M / tp / 1e9, "q_mean": qpm},
         "speedup_vs_plain": tp / tb,
         "q_loss_pct": float((qpm - qbm) / abs(qpm) * 100) if qpm else 0.0,
@@ -510,8 +533,9 @@ def time_sweeps(cd, torch, G, lab, k: int, steps: int, stream):
 def end_to_end(cd, torch, g, k: int, steps: int, out_dev):
     """The same step through the C ABI with pinned host buffers (the call
     copies the CSR and labels in and the labels out); returns the e2e object.
-    Beside it, the time of the bare host-to-device copies of the same bytes
-    (the bound of this path)."""
+    Before each timed call, the bare host-to-device copy of the same bytes is
+    timed too (the bound of this path at that moment: the host link's rate
+    varies on a shared machine, from about 210 GB/s down to a sixth of it)."""
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     ho, hc, hw = pin(g.offsets), pin(g.cols), pin(g.w.view(np.int32))
     hl = pin(np.arange(g.n, dtype=np.uint32).view(np.int32))
@@ -519,40 +543,41 @@ def end_to_end(cd, torch, g, k: int, steps: int, out_dev):
     Gh = cd.Graph(g.n, ho.numpy(), hc.numpy(), hw.numpy().view(np.uint32))
     lab_h, out_h = hl.numpy().view(np.uint32), hout.numpy().view(np.uint32)
     ph = cd.make_params(k=k, stream=torch.cuda.current_stream().cuda_stream)
+    dev = [torch.empty(x.shape, dtype=x.dtype, device="cuda") for x in (ho, hc, hw, hl)]
+
+    def bare_copy_ms():
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for d, h in zip(dev, (ho, hc, hw, hl)):
+            d.copy_(h, non_blocking=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
     for _ in range(3):  # warm-up: the first calls grow the device memory pool
         cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
+        bare_copy_ms()
     torch.cuda.synchronize()
-    per, phases = [], []
+    per, phases, copies = [], [], []
     for _ in range(steps):
+        copies.append(bare_copy_ms())
         t0 = time.perf_counter()
         cd.cd_sweep(Gh, ph, cd.MODE_LOUVAIN, lab_h, labels_out=out_h)
         per.append((time.perf_counter() - t0) * 1e3)
         phases.append([round(x, 2) for x in cd.cd_last_stats().phase_ms])
-    # bare copies of the same bytes (three pinned tensors and the labels)
-    dev = [torch.empty(x.shape, dtype=x.dtype, device="cuda") for x in (ho, hc, hw, hl)]
-    for _ in range(2):
-        for d, h in zip(dev, (ho, hc, hw, hl)):
-            d.copy_(h, non_blocking=True)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for d, h in zip(dev, (ho, hc, hw, hl)):
-        d.copy_(h, non_blocking=True)
-    ev1.record()
-    torch.cuda.synchronize()
-    copy_ms = ev0.elapsed_time(ev1)
     del dev
     h2d = g.offsets.nbytes + g.cols.nbytes + g.w.nbytes + lab_h.nbytes
     ms = float(np.mean(per))
     return {"value": g.nnz / (ms * 1e-3) / 1e9, "unit": "GTEPS",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out_h.nbytes),
-            "ms_per_step": [round(x, 3) for x in per], "copy_bound_ms": copy_ms,
+            "ms_per_step": [round(x, 3) for x in per], "median_ms": float(np.median(per)),
+            "copy_bound_ms_per_step": [round(x, 3) for x in copies],
+            "vs_copy_bound_per_step": [round(a / b, 3) for a, b in zip(per, copies)],
             "phase_ms_per_step": phases,
             "phases": "host clock at the end of: staging, host-input checks, degrees/buckets/totals, the call",
-            "vs_copy_bound": ms / copy_ms,
             "note": "cd_sweep with pinned host CSR and labels: host-to-device copies, the sweep and the "
-                    "device-to-host labels inside each timed call; copy_bound_ms = bare pinned copies of "
-                    "the same input bytes",
+                    "device-to-host labels inside each timed call; before each call, the bare pinned "
+                    "copies of the same input bytes are timed (copy_bound_ms_per_step)",
             "matches_device_run": bool(np.array_equal(out_h, out_dev.cpu().numpy().view(np.uint32)))}
 
 

@@ -86,7 +86,11 @@ typedef struct cd_csr {
  * S[s] <- merge(S[s], S[s + o]) for o = lanes/2, ..., 1 and all s < o, where
  * merge(A, B) feeds every slot of B with a positive value, in slot order, to
  * A as one Algorithm 1 update.  lanes[b] is a power of two in [1, 256];
- * deg_max ascending; vec must be 4.
+ * deg_max ascending; vec must be 4.  blocks_per_sm (launch shape only, no
+ * effect on any result): 0 = the MG sweep kernel gets one 256-thread block
+ * per group of rows ("virtual block"); n in [1, 8] = it gets n blocks per SM,
+ * which stay resident and take the virtual blocks in turn, longest rows
+ * first (a persistent launch).
  */
 #define CD_MAX_BUCKETS 16
 typedef struct cd_schedule {
@@ -94,6 +98,7 @@ typedef struct cd_schedule {
     int32_t vec;
     int64_t deg_max[CD_MAX_BUCKETS];
     int32_t lanes[CD_MAX_BUCKETS];
+    int32_t blocks_per_sm;
 } cd_schedule;
 
 /* Learned skip proposal (an addition to the paper's method, which has no
@@ -280,12 +285,14 @@ typedef struct cd_tune_report {
 /* Autotuner of the batched form (an addition to the paper's method; it
  * changes no arithmetic, only the schedule and k): packs the graphs as
  * cd_louvain_batched does, then for every candidate sketch size ks[i] (nks
- * <= CD_TUNE_MAX_K, each a valid k) tunes the streams per degree band of
- * the schedule (deg_max bands of p->sched or the default) by coordinate
- * descent on timed sweeps of the whole batch from singleton labels (each
- * band, longest rows first, tries half and twice its streams and keeps a
- * change that is at least 2% faster; median of 3 CUDA-event timings), and
- * runs batched Louvain with the tuned schedule.  The choice is the fastest
+ * <= CD_TUNE_MAX_K, each a valid k) tunes the schedule (p->sched or the
+ * default) by coordinate descent on timed sweeps of the whole batch from
+ * singleton labels, keeping a change only when it is at least 2% faster
+ * (median of 3 CUDA-event timings): the streams per degree band (each band,
+ * longest rows first, tries half and twice its streams), then the band
+ * thresholds (each deg_max tries 3/4 and 3/2 of its value, order kept), then
+ * the launch shape (blocks_per_sm 0, 4, 2); and runs batched Louvain with
+ * the tuned schedule.  The choice is the fastest
  * candidate whose mean modularity is within q_tol (relative) of the best
  * candidate's.  sched_out, k_out (host) receive it; report (host, may be
  * NULL) the timings.  Timings vary from run to run, so the choice may too;

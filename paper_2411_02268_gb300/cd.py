@@ -36,7 +36,8 @@ class CSR(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("nbuckets", ctypes.c_int32), ("vec", ctypes.c_int32),
-                ("deg_max", ctypes.c_int64 * MAX_BUCKETS), ("lanes", ctypes.c_int32 * MAX_BUCKETS)]
+                ("deg_max", ctypes.c_int64 * MAX_BUCKETS), ("lanes", ctypes.c_int32 * MAX_BUCKETS),
+                ("blocks_per_sm", ctypes.c_int32)]
 
     def as_lists(self):
         nb = self.nbuckets
@@ -243,9 +244,9 @@ def make_params(k=8, subtract=0, tolerance=0.01, tolerance_drop=10.0, aggregatio
     return p
 
 
-def schedule_from(deg_max, lanes, vec=4) -> Schedule:
+def schedule_from(deg_max, lanes, vec=4, blocks_per_sm=0) -> Schedule:
     s = Schedule()
-    s.nbuckets, s.vec = len(lanes), vec
+    s.nbuckets, s.vec, s.blocks_per_sm = len(lanes), vec, int(blocks_per_sm)
     for b, (d, l) in enumerate(zip(deg_max, lanes)):
         s.deg_max[b], s.lanes[b] = int(d), int(l)
     return s

@@ -172,6 +172,7 @@ void default_schedule(int k, cd_schedule* s) {
 
 int check_schedule(const cd_schedule* s) {
     if (s->nbuckets < 1 || s->nbuckets > CD_MAX_BUCKETS || s->vec != 4) return CD_EINVAL;
+    if (s->blocks_per_sm < 0 || s->blocks_per_sm > 8) return CD_EINVAL;
     for (int b = 0; b < s->nbuckets; ++b) {
         int L = s->lanes[b];
         if (L < 1 || L > 256 || (L & (L - 1))) return CD_EINVAL;
@@ -219,6 +220,7 @@ BucketTable table_from(const cd_schedule& s) {
     std::memset(&bt, 0, sizeof(bt));
     bt.nb = s.nbuckets;
     for (int b = 0; b < s.nbuckets; ++b) { bt.deg_max[b] = s.deg_max[b]; bt.lanes[b] = s.lanes[b]; }
+    bt.resident = s.blocks_per_sm;
     return bt;
 }
 
@@ -357,7 +359,15 @@ SweepArgs make_args(const Level& L, const uint32_t* labels_in, uint32_t* labels_
 // Launches one sweep (all buckets) on stream s.
 int launch_sweep(const Level& L, const SweepArgs& a, int k, Scratch& sc, cudaStream_t s) {
     if (k > 0) {
-        CD_CUDA(launch_sweep_mg(a, k, L.wide, L.bt.bbegin[L.bt.nb], s));
+        int64_t nblocks = L.bt.bbegin[L.bt.nb];
+        if (L.bt.resident > 0) {
+            // a resident grid striding over the virtual blocks
+            int dev = 0, sms = 0;
+            CD_CUDA(cudaGetDevice(&dev));
+            CD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            nblocks = std::min<int64_t>(nblocks, (int64_t)sms * L.bt.resident);
+        }
+        CD_CUDA(launch_sweep_mg(a, k, L.wide, nblocks, s));
         return CD_OK;
     }
     for (int b = 0; b < kExactBuckets; ++b) {
@@ -1670,6 +1680,34 @@ int cd_autotune(const cd_csr* graphs, int ngraphs, const cd_params* p, const int
                             best = ms;
                             cur = t;
                         }
+                    }
+                }
+                // band thresholds: each finite deg_max moves to 3/4 or 3/2 of
+                // its value when the order of the bands allows it
+                for (int b = 0; b + 1 < cur.nbuckets; ++b) {
+                    const int64_t d0 = cur.deg_max[b];
+                    for (int64_t cand : {d0 * 3 / 4, d0 * 3 / 2}) {
+                        const int64_t lo = b > 0 ? cur.deg_max[b - 1] : 0;
+                        if (cand <= lo || cand >= cur.deg_max[b + 1] || cand == d0) continue;
+                        cd_schedule t = cur;
+                        t.deg_max[b] = cand;
+                        double ms = 0.0;
+                        CD_TRY(time_sweep(t, k, &ms));
+                        if (ms < 0.98 * best) {
+                            best = ms;
+                            cur = t;
+                        }
+                    }
+                }
+                // launch shape: one block per virtual block, or a resident grid
+                for (int r : {4, 2}) {
+                    cd_schedule t = cur;
+                    t.blocks_per_sm = r;
+                    double ms = 0.0;
+                    CD_TRY(time_sweep(t, k, &ms));
+                    if (ms < 0.98 * best) {
+                        best = ms;
+                        cur = t;
                     }
                 }
             }

@@ -42,7 +42,8 @@ struct Globals {
 // and is processed by grid blocks [bbegin[b], bbegin[b+1]).
 struct BucketTable {
     int nb;
-    int qmul;  // lanes per stream: k / 8 for the slot form of k >= 32, else 1 (0 reads as 1)
+    int qmul;      // lanes per stream: k / 8 for the slot form of k >= 32, else 1 (0 reads as 1)
+    int resident;  // MG sweep launch: blocks per SM that stride over the virtual blocks (0 = one each)
     int lanes[CD_MAX_BUCKETS];
     int64_t deg_max[CD_MAX_BUCKETS];
     int64_t vbegin[CD_MAX_BUCKETS + 1];

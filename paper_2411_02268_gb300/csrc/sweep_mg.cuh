@@ -52,25 +52,31 @@ struct Sketch {
     // empty slot (conditional, mode 0) subtract w from every slot, clamping
     // at 0.
     __device__ __forceinline__ void update(uint32_t c, VT w, int mode) {
+        // is c held?  (compares only; the slot gets w on the hit path)
         bool has = false;
 #pragma unroll
-        for (int p = 0; p < K; ++p) {
-            const bool m = key[p] == c;
-            t[p] += m ? w : (VT)0;
-            has |= m;
+        for (int p = 0; p < K; ++p) has |= key[p] == c;
+        if (has) {
+#pragma unroll
+            for (int p = 0; p < K; ++p) t[p] += key[p] == c ? w : (VT)0;
+            return;
         }
-        if (!has) {
-            if (mode) {
+        if (mode) {
 #pragma unroll
-                for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
-                lossy = true;
-            }
-            bool done = insert_top(c, w);
-            if (!done && !mode) {
+            for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
+            lossy = true;
+        }
+        // a free slot takes c; with none, the conditional rule lowers every
+        // slot (the downward search runs only when it will succeed)
+        bool free = false;
 #pragma unroll
-                for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
-                lossy = true;
-            }
+        for (int p = 0; p < K; ++p) free |= t[p] == 0;
+        if (free) {
+            insert_top(c, w);
+        } else if (!mode) {
+#pragma unroll
+            for (int p = 0; p < K; ++p) t[p] = (t[p] > w ? t[p] : w) - w;
+            lossy = true;
         }
     }
 
@@ -703,10 +709,11 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks<K, VT>()) k_sweep_mg(
     __shared__ EpiSmem esm;
     // Virtual blocks, the longest rows first, so that they start at once and
     // overlap with the many short rows instead of trailing the launch.  A
-    // full sweep runs one virtual block per grid block; a skip sweep over the
-    // compacted list (ranges on the device) runs a smaller grid that strides
-    // over its virtual blocks.
-    const int64_t nvirt = a.dr ? a.dr->bbegin[a.bt.nb] : (int64_t)gridDim.x;
+    // full sweep runs one virtual block per grid block unless the schedule
+    // asks for a resident grid; a skip sweep over the compacted list (ranges
+    // on the device) runs a smaller grid; both stride over the virtual
+    // blocks.
+    const int64_t nvirt = a.dr ? a.dr->bbegin[a.bt.nb] : a.bt.bbegin[a.bt.nb];
     for (int64_t j = blockIdx.x; j < nvirt; j += gridDim.x) {
         if (j != (int64_t)blockIdx.x) __syncthreads();  // the previous virtual block is done with shared memory
         const int64_t blk = nvirt - 1 - j;

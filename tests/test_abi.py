@@ -46,7 +46,7 @@ def test_struct_layout_matches_header(cd, tmp_path):
 #include "cd.h"
 int main(void) {
   printf("csr %zu %zu %zu\n", sizeof(cd_csr), offsetof(cd_csr, weights), offsetof(cd_csr, memory));
-  printf("sched %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes));
+  printf("sched %zu %zu %zu %zu\n", sizeof(cd_schedule), offsetof(cd_schedule, deg_max), offsetof(cd_schedule, lanes), offsetof(cd_schedule, blocks_per_sm));
   printf("params %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cd_params), offsetof(cd_params, sched), offsetof(cd_params, stream), offsetof(cd_params, timing), offsetof(cd_params, colors), offsetof(cd_params, one_scan), offsetof(cd_params, capture));
   printf("stats %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cd_stats), offsetof(cd_stats, sweep_kernel_ms), offsetof(cd_stats, entries_scanned), offsetof(cd_stats, cuda_error), offsetof(cd_stats, kernel_launches), offsetof(cd_stats, candidates), offsetof(cd_stats, phase_ms));
   printf("mlp %zu %zu\n", sizeof(cd_mlp), offsetof(cd_mlp, b2));
@@ -60,7 +60,7 @@ int main(void) {
     C = ctypes
     exp = [
         f"csr {C.sizeof(cd.CSR)} {cd.CSR.weights.offset} {cd.CSR.memory.offset}",
-        f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset}",
+        f"sched {C.sizeof(cd.Schedule)} {cd.Schedule.deg_max.offset} {cd.Schedule.lanes.offset} {cd.Schedule.blocks_per_sm.offset}",
         f"params {C.sizeof(cd.Params)} {cd.Params.sched.offset} {cd.Params.stream.offset} {cd.Params.timing.offset} {cd.Params.colors.offset} {cd.Params.one_scan.offset} {cd.Params.capture.offset}",
         f"stats {C.sizeof(cd.Stats)} {cd.Stats.sweep_kernel_ms.offset} {cd.Stats.entries_scanned.offset} {cd.Stats.cuda_error.offset} {cd.Stats.kernel_launches.offset} {cd.Stats.candidates.offset} {cd.Stats.phase_ms.offset}",
         f"mlp {C.sizeof(cd.MLP)} {cd.MLP.b2.offset}",

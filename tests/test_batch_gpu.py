@@ -145,6 +145,9 @@ def test_autotune_picks_valid_schedule_and_k(env, graphs):
     dev = [cd.Graph.to_device(g) for g in graphs]
     sched, k, rep = cd.cd_autotune(dev, cd.make_params(k=8), ks=(4, 8, 16), q_tol=0.005)
     assert k in (4, 8, 16) and 0 <= rep.chosen < 3 and rep.trials > 10
+    # thresholds ascending, launch shape valid
+    dm = list(sched.deg_max[:sched.nbuckets])
+    assert all(a < b for a, b in zip(dm, dm[1:])) and sched.blocks_per_sm in (0, 2, 4)
     assert rep.sweep_ms[0] <= rep.default_ms * 1.10
     qbest = max(rep.q_mean[:3])
     assert rep.q_mean[rep.chosen] >= qbest - 0.005 * abs(qbest)

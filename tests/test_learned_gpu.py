@@ -193,3 +193,32 @@ def test_skip_rules_same_with_graph_replay(env):
                                                      capture=capture))
             outs.append((lab.cpu().numpy(), q, cd.cd_last_stats().entries_scanned))
         assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1:] == outs[1][1:]
+
+
+def test_learned_skip_faster_on_large_grid(env):
+    """Wall time, not only entries: on the 4096 x 4096 grid with 2% of its
+    edges rewired (16.8 M vertices), Louvain with the learned proposal
+    finishes faster than the plain driver (both replaying CUDA graphs), at a
+    modularity loss within 0.5%.  Medians of three runs; the margin (3%)
+    is well inside the measured gain (about 1.2x) and covers timing noise."""
+    import time
+    cd, torch = env
+    m, *_ = trained_model(cd, torch)
+    G = cd.Graph.to_device(gen.grid(4096, 4096, 0.02, 16, seed=1))
+
+    def run(**kw):
+        ts, q = [], None
+        cd.cd_louvain(G, cd.make_params(k=8, **kw))  # warm-up
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, q = cd.cd_louvain(G, cd.make_params(k=8, **kw))
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        return float(np.median(ts)), q
+
+    t_plain, q_plain = run()
+    t_learn, q_learn = run(skip_rule=1, skip_threshold=0.02, skip_model=m)
+    print(f"grid4096: plain {t_plain * 1e3:.1f} ms Q={q_plain:.5f}; learned {t_learn * 1e3:.1f} ms Q={q_learn:.5f}")
+    assert q_learn >= q_plain - 0.005 * abs(q_plain)
+    assert t_learn < 0.97 * t_plain

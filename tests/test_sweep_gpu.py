@@ -448,3 +448,18 @@ def test_candidate_count_matches_oracle(env, k):
             keys, vals = oracle.row_sketch(g, int(i), lab, k, osched)
             want += int(np.count_nonzero((vals > 0) & (keys != lab[i])))
         assert got == want
+
+
+@pytest.mark.parametrize("k", [8, 16, 64])
+@pytest.mark.parametrize("bpsm", [1, 4])
+def test_resident_grid_same_results(env, k, bpsm):
+    """A schedule's blocks_per_sm only changes the launch shape (a resident
+    grid striding over the virtual blocks): every sweep result is the
+    oracle's, as with one block per virtual block."""
+    cd, torch = env
+    for gname in ("rmat12_w16", "sbm10k"):
+        g = GRAPHS[gname]()
+        deg, lanes, vec = cd.cd_default_schedule(k).as_lists()
+        s = cd.schedule_from(deg, lanes, vec, blocks_per_sm=bpsm)
+        for _, lab in label_states(g, 6):
+            check(cd, torch, g, lab, oracle.MODE_LOUVAIN, k, sched=s)
