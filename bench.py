@@ -99,7 +99,7 @@ def kernel_source_hash(k: int = 8) -> str:
     """Hash of the sources that define the k-slot sweep kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_02268_gb300", "csrc")
-    for f in ("cd_internal.cuh", "sweep_mg.cuh", f"sweep_k{k}.cu"):
+    for f in ("cd_internal.cuh", "sweep_mg.cuh", "sweep_slots.cuh", f"sweep_k{k}.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -581,6 +581,30 @@ def end_to_end(cd, torch, g, k: int, steps: int, out_dev):
             "matches_device_run": bool(np.array_equal(out_h, out_dev.cpu().numpy().view(np.uint32)))}
 
 
+def profile_case(args):
+    """A small, fixed invocation of one entry point for single-kernel ncu
+    captures (`--case`): two calls, the second being the one to capture."""
+    import torch
+    from paper_2411_02268_gb300 import cd
+    torch.cuda.set_device(0)
+    g = make_graph(args.workload)
+    G = cd.Graph.to_device(g)
+    lab = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        if args.case == "sweep":        # the MG sweep (or the exact hashtable with --k 0)
+            cd.cd_sweep(G, cd.make_params(k=args.k), cd.MODE_LOUVAIN, lab)
+        elif args.case == "aggregate":  # renumbering and super-graph of 16-vertex blocks
+            cd.cd_aggregate(G, torch.div(lab, 16, rounding_mode="floor"))
+        elif args.case == "mlp":        # the skip model's gradient on n random feature rows
+            m = cd.MLP.init(seed=1)
+            x = torch.from_numpy(rng.random((g.n, 8)).astype(np.float16)).cuda()
+            y = torch.from_numpy((rng.random(g.n) < 0.3).astype(np.uint8)).cuda()
+            cd.cd_mlp_gradient(x, y, m)
+    torch.cuda.synchronize()
+    print(f"case {args.case} on {args.workload}: n={g.n} nnz={g.nnz} k={args.k}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,7 +630,12 @@ def main():
                     help="after the warm-up steps, keep stepping (untimed) for this long")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="graphs in the batched-vs-plain comparison (0 = skip it)")
+    ap.add_argument("--case", default=None, choices=["sweep", "aggregate", "mlp"],
+                    help="run one small invocation for a single-kernel ncu capture and exit")
     args = ap.parse_args()
+    if args.case:
+        profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
 

@@ -201,19 +201,27 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const __half* __restrict__ x, 
     if (t == 0) loss_partial[blockIdx.x] = lsum[0];
 }
 
-// Sums the block partials in block order (deterministic) and divides by n.
-__global__ void k_mlp_grad_sum(const float* __restrict__ partial, const float* __restrict__ loss_partial,
-                               int64_t nblocks, int64_t n, float* __restrict__ grad, float* __restrict__ loss) {
+// Sums the block partials and divides by n: block p takes parameter p (the
+// last block the loss); thread t adds the partials of blocks t, t + 256, ...
+// in that order, then the 256 sums are added by a fixed tree.  The order of
+// every addition is fixed, so the result is the same on every run.
+__global__ void __launch_bounds__(256) k_mlp_grad_sum(const float* __restrict__ partial,
+                                                      const float* __restrict__ loss_partial, int64_t nblocks,
+                                                      int64_t n, float* __restrict__ grad, float* __restrict__ loss) {
+    __shared__ double sh[256];
+    const int p = blockIdx.x;  // 0 .. kGradLen (kGradLen = the loss)
     const int t = threadIdx.x;
-    if (t < kGradLen) {
-        double s = 0.0;
-        for (int64_t b = 0; b < nblocks; ++b) s += partial[b * kGradLen + t];
-        grad[t] = (float)(s / (double)n);
+    double s = 0.0;
+    for (int64_t b = t; b < nblocks; b += 256) s += p < kGradLen ? partial[b * kGradLen + p] : loss_partial[b];
+    sh[t] = s;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
+        __syncthreads();
     }
     if (t == 0) {
-        double s = 0.0;
-        for (int64_t b = 0; b < nblocks; ++b) s += loss_partial[b];
-        *loss = (float)(s / (double)n);
+        if (p < kGradLen) grad[p] = (float)(sh[0] / (double)n);
+        else *loss = (float)(sh[0] / (double)n);
     }
 }
 
@@ -300,7 +308,7 @@ cudaError_t launch_mlp_grad(const void* x, const uint8_t* y, int64_t n, const fl
     note_launch();
     k_mlp_grad<<<(unsigned)nb, 256, 0, s>>>(static_cast<const __half*>(x), y, n, param, partial, loss_partial);
     note_launch();
-    k_mlp_grad_sum<<<1, 352, 0, s>>>(partial, loss_partial, nb, n, grad, loss);
+    k_mlp_grad_sum<<<kGradLen + 1, 256, 0, s>>>(partial, loss_partial, nb, n, grad, loss);
     return cudaGetLastError();
 }
 
