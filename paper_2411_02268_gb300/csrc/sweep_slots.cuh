@@ -130,8 +130,15 @@ __device__ __forceinline__ void scan_chunks_sync(const SweepArgs& a, int64_t fir
                     if (ok[u]) ok[u] = __ldg(a.bound + cur.c[u]) == bi;
             }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) f(labs[u], ws[u], ok[u]);
+        // one copy of f for the four entries (f holds the votes: a smaller
+        // body keeps the instruction cache warm)
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            f(labs[0], ws[0], ok[0]);
+            labs[0] = labs[1]; labs[1] = labs[2]; labs[2] = labs[3];
+            ws[0] = ws[1]; ws[1] = ws[2]; ws[2] = ws[3];
+            ok[0] = ok[1]; ok[1] = ok[2]; ok[2] = ok[3];
+        }
     }
 }
 
@@ -292,13 +299,10 @@ __device__ __forceinline__ Outcome slot_body(const SweepArgs& a, int64_t vi, boo
         // their own column, which is in range, and ignore it)
         const int src0 = recv ? (int)threadIdx.x - q + o * Q : (int)threadIdx.x - q;
 #pragma unroll 1
-        for (int q2 = 0; q2 < Q; ++q2) {
-#pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                const uint32_t bk = sm.k[p][src0 + q2];
-                const VT bv = sm.v[p][src0 + q2];
-                lossy |= slot_update<Q, VT>(sk, bk, bv, recv && bv > 0, unc, g);
-            }
+        for (int j = 0; j < 8 * Q; ++j) {  // the partner's slots in slot order: part j / 8, slot j % 8
+            const uint32_t bk = sm.k[j & 7][src0 + (j >> 3)];
+            const VT bv = sm.v[j & 7][src0 + (j >> 3)];
+            lossy |= slot_update<Q, VT>(sk, bk, bv, recv && bv > 0, unc, g);
         }
         if (recv) lossy |= sm.lossy[src0] != 0;
         row_sync<T>();
