@@ -274,11 +274,25 @@ struct Outcome {
 
 // Feeds the live slots of a partner sketch (keys pk, values pv) to s.
 template <int K, typename VT, typename U>
-__device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk)[K], const VT (&pv)[K],
+__device__ __forceinline__ void merge_into(Sketch<K, VT>& s, const uint32_t (&pk_in)[K], const VT (&pv_in)[K],
                                            bool plossy, U unc) {
+    if constexpr (K >= 16) {
+        // one copy of the update: the partner's slots rotate through slot 0
+        uint32_t pk[K];
+        VT pv[K];
 #pragma unroll
-    for (int p = 0; p < K; ++p)
-        if (pv[p] > 0) s.update(pk[p], pv[p], unc);
+        for (int p = 0; p < K; ++p) { pk[p] = pk_in[p]; pv[p] = pv_in[p]; }
+#pragma unroll 1
+        for (int p = 0; p < K; ++p) {
+            if (pv[0] > 0) s.update(pk[0], pv[0], unc);
+#pragma unroll
+            for (int q = 0; q + 1 < K; ++q) { pk[q] = pk[q + 1]; pv[q] = pv[q + 1]; }
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < K; ++p)
+            if (pv_in[p] > 0) s.update(pk_in[p], pv_in[p], unc);
+    }
     s.lossy |= plossy;
 }
 
