@@ -596,6 +596,8 @@ def profile_case(args):
             cd.cd_sweep(G, cd.make_params(k=args.k), cd.MODE_LOUVAIN, lab)
         elif args.case == "aggregate":  # renumbering and super-graph of 16-vertex blocks
             cd.cd_aggregate(G, torch.div(lab, 16, rounding_mode="floor"))
+        elif args.case == "louvain":    # a whole Louvain detection (all passes)
+            cd.cd_louvain(G, cd.make_params(k=args.k))
         elif args.case == "mlp":        # the skip model's gradient on n random feature rows
             m = cd.MLP.init(seed=1)
             x = torch.from_numpy(rng.random((g.n, 8)).astype(np.float16)).cuda()
@@ -630,7 +632,7 @@ def main():
                     help="after the warm-up steps, keep stepping (untimed) for this long")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="graphs in the batched-vs-plain comparison (0 = skip it)")
-    ap.add_argument("--case", default=None, choices=["sweep", "aggregate", "mlp"],
+    ap.add_argument("--case", default=None, choices=["sweep", "aggregate", "louvain", "mlp"],
                     help="run one small invocation for a single-kernel ncu capture and exit")
     args = ap.parse_args()
     if args.case:

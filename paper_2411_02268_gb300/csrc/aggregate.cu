@@ -136,40 +136,108 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int sh
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ p1,
-                                const uint32_t* __restrict__ p2, int64_t n, int shift,
-                                const uint32_t* __restrict__ offs, int64_t ntiles, uint32_t* __restrict__ key_o,
-                                uint32_t* __restrict__ p1_o, uint32_t* __restrict__ p2_o) {
-    __shared__ uint32_t wc[8][256];
-    __shared__ uint32_t run[256];
+// The tile's entries are first placed in shared memory in their sorted order
+// (digit, then original order), then written out so that consecutive threads
+// write consecutive positions of one digit's run: the global writes coalesce
+// (placing every entry straight at its global position scattered 4 bytes per
+// 32-byte sector over three arrays).  Each warp owns a contiguous slice of
+// 1024 entries of the tile: it counts its digits, a prefix over the warps
+// gives each warp where its entries of every digit start, and the warp then
+// places its slice in order (rank among equal digits of a step, steps in
+// order), so the sort stays stable with four block-wide barriers per tile.
+// The tile's digit counts and output starts come from the scanned histogram
+// (consecutive exclusive offsets in digit-major order).
+constexpr int kRadixSmem = 3 * kRadixTile * (int)sizeof(uint32_t);
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixSlice = kRadixTile / kRadixWarps;  // entries per warp
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const uint32_t* __restrict__ key, const uint32_t* __restrict__ p1, const uint32_t* __restrict__ p2, int64_t n,
+    int shift, const uint32_t* __restrict__ offs, int64_t ntiles, uint32_t* __restrict__ key_o,
+    uint32_t* __restrict__ p1_o, uint32_t* __restrict__ p2_o) {
+    extern __shared__ __align__(16) uint32_t tile_buf[];  // keys, p1, p2 of the tile in sorted order
+    uint32_t* sk = tile_buf;
+    uint32_t* s1 = tile_buf + kRadixTile;
+    uint32_t* s2 = tile_buf + 2 * kRadixTile;
+    __shared__ uint32_t wcnt[kRadixWarps][256];  // per warp: count, then the running start, of each digit
+    __shared__ uint32_t tstart[256];  // where each digit's run starts in the tile
+    __shared__ uint32_t gbase[256];   // where it starts in the output
+    __shared__ uint32_t wsum[kRadixWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = 0;
-    int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    for (int r = 0; r < kRadixRounds; ++r) {
+    const int64_t tile = blockIdx.x;
+    const int64_t base = tile * kRadixTile;
+    const int tn = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
+    {
+        // digit d: output start and count of this tile, and its start in the tile
+        const int d = threadIdx.x;
+        const int64_t idx = (int64_t)d * ntiles + tile;
+        const uint32_t g0 = offs[idx];
+        const uint32_t g1 = idx + 1 < 256 * ntiles ? offs[idx + 1] : (uint32_t)n;
+        gbase[d] = g0;
+        uint32_t x = g1 - g0;  // inclusive scan of the counts over the digits
 #pragma unroll
-        for (int q = 0; q < 8; ++q) wc[q][threadIdx.x] = 0;
-        __syncthreads();
-        int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
-        bool ok = i < n;
-        uint32_t k = ok ? key[i] : 0u;
-        int dgt = ok ? (int)((k >> shift) & 255u) : -1;
-        unsigned peers = __match_any_sync(0xffffffffu, dgt);
-        unsigned rank = __popc(peers & ((1u << lane) - 1u));
-        if (ok && rank == 0) wc[warp][dgt] = __popc(peers);
-        __syncthreads();
-        if (ok) {
-            uint32_t pos = offs[(int64_t)dgt * ntiles + blockIdx.x] + run[dgt] + rank;
-            for (int q = 0; q < warp; ++q) pos += wc[q][dgt];
-            key_o[pos] = k;
-            p1_o[pos] = p1[i];
-            p2_o[pos] = p2[i];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        __syncthreads();
-        uint32_t t = 0;
+        if (lane == 31) wsum[warp] = x;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += wc[q][threadIdx.x];
-        run[threadIdx.x] += t;
+        for (int q = 0; q < kRadixWarps; ++q) wcnt[q][d] = 0;
         __syncthreads();
+        uint32_t before = 0;
+        for (int q = 0; q < warp; ++q) before += wsum[q];
+        tstart[d] = before + x - (g1 - g0);
+    }
+    const int j0 = warp * kRadixSlice;
+    // count the digits of this warp's slice
+    for (int t = 0; t < kRadixSlice; t += 32) {
+        const int j = j0 + t + lane;
+        const bool ok = j < tn;
+        const int dgt = ok ? (int)((key[base + j] >> shift) & 255u) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, dgt);
+        if (ok && (peers & ((1u << lane) - 1u)) == 0) wcnt[warp][dgt] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // per digit: exclusive prefix over the warps, from the digit's tile start
+        const int d = threadIdx.x;
+        uint32_t run = tstart[d];
+#pragma unroll
+        for (int q = 0; q < kRadixWarps; ++q) {
+            const uint32_t c = wcnt[q][d];
+            wcnt[q][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // place the slice in order
+    for (int t = 0; t < kRadixSlice; t += 32) {
+        const int j = j0 + t + lane;
+        const bool ok = j < tn;
+        const int64_t i = base + j;
+        const uint32_t k = ok ? key[i] : 0u;
+        const int dgt = ok ? (int)((k >> shift) & 255u) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, dgt);
+        const unsigned below = peers & ((1u << lane) - 1u);
+        if (ok) {
+            const uint32_t pos = wcnt[warp][dgt] + __popc(below);
+            sk[pos] = k;
+            s1[pos] = p1[i];
+            s2[pos] = p2[i];
+        }
+        __syncwarp();
+        if (ok && below == 0) wcnt[warp][dgt] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < tn; j += kRadixThreads) {
+        const uint32_t k = sk[j];
+        const int d = (int)((k >> shift) & 255u);
+        const uint32_t pos = gbase[d] + (uint32_t)j - tstart[d];
+        key_o[pos] = k;
+        p1_o[pos] = s1[j];
+        p2_o[pos] = s2[j];
     }
 }
 
@@ -182,18 +250,50 @@ __global__ void k_heads(const uint32_t* __restrict__ src, const uint32_t* __rest
 }
 
 // uidx = exclusive scan of heads; unique entry u = uidx[e] for its first e.
+// The sorted entries of one key are consecutive, so the lanes of a warp sum
+// their runs with a segmented shuffle reduction and the first lane of each
+// run piece adds it to wsum[u]: one atomic per run and warp instead of one
+// per entry (after a pass most entries of a community fall into a few long
+// runs, whose per-entry atomics would serialise on one address).  Integer
+// sums: the order does not matter.
 __global__ void k_segsum(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst,
                          const uint32_t* __restrict__ w, const uint32_t* __restrict__ heads,
                          const uint32_t* __restrict__ uidx, int64_t n, int32_t* __restrict__ cols_out,
                          unsigned long long* __restrict__ wsum, uint32_t* __restrict__ rowcnt) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    uint32_t u = uidx[e] + heads[e] - 1u;  // index of this entry's unique key
-    atomicAdd(&wsum[u], (unsigned long long)w[e]);
-    if (heads[e]) {
-        cols_out[u] = (int32_t)dst[e];
-        atomicAdd(&rowcnt[src[e]], 1u);
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = e < n;
+    uint32_t head = 0, u = 0xFFFFFFFFu;  // past the end: a key of its own
+    unsigned long long v = 0;
+    if (valid) {
+        head = heads[e];
+        u = uidx[e] + head - 1u;  // index of this entry's unique key
+        v = w[e];
     }
+    // sum each lane's run to its right within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v2 = __shfl_down_sync(0xffffffffu, v, o);
+        const uint32_t u2 = __shfl_down_sync(0xffffffffu, u, o);
+        if (lane + o < 32 && u2 == u) v += v2;
+    }
+    const uint32_t uprev = __shfl_up_sync(0xffffffffu, u, 1);
+    // distinct keys per row: the heads of one row are consecutive too, so
+    // they are counted the same way (a hub community has millions of
+    // distinct neighbour communities, one atomic each would serialise)
+    const uint32_t r = valid ? src[e] : 0xFFFFFFFFu;
+    uint32_t c = head;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t c2 = __shfl_down_sync(0xffffffffu, c, o);
+        const uint32_t r2 = __shfl_down_sync(0xffffffffu, r, o);
+        if (lane + o < 32 && r2 == r) c += c2;
+    }
+    const uint32_t rprev = __shfl_up_sync(0xffffffffu, r, 1);
+    if (!valid) return;
+    if (lane == 0 || uprev != u) atomicAdd(&wsum[u], v);
+    if (head) cols_out[u] = (int32_t)dst[e];
+    if ((lane == 0 || rprev != r) && c) atomicAdd(&rowcnt[r], c);
 }
 
 __global__ void k_narrow(const unsigned long long* __restrict__ wsum, int64_t m, uint32_t* __restrict__ w_out,
@@ -216,6 +316,10 @@ int bits_for(int64_t nc) {
 // with ties in input order.  On return the sorted arrays are in (src, dst, w)
 // (the buffers may have been swapped with the *2 ones).
 cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_dst, Globals* glob, cudaStream_t s) {
+    {
+        cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kRadixSmem);
+        if (e != cudaSuccess) return e;
+    }
     int64_t nt = radix_tiles(nnz);
     int64_t hn = nt * 256;
     for (int which = 0; which < 2; ++which) {
@@ -230,8 +334,8 @@ cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_d
             cudaError_t e = launch_exclusive_scan_u32(a.hist, a.hist, hn, a.tiles, &glob->count, s);
             if (e != cudaSuccess) return e;
             note_launch();
-            k_radix_scatter<<<(unsigned)nt, kRadixThreads, 0, s>>>(key, p1, a.w, nnz, shift, a.hist, nt, key_o,
-                                                                    p1_o, a.w2);
+            k_radix_scatter<<<(unsigned)nt, kRadixThreads, kRadixSmem, s>>>(key, p1, a.w, nnz, shift, a.hist, nt,
+                                                                             key_o, p1_o, a.w2);
             std::swap(a.src, a.src2);
             std::swap(a.dst, a.dst2);
             std::swap(a.w, a.w2);
