@@ -385,9 +385,7 @@ int cd_trace(const cd_csr* g, const cd_params* p, double sample_rate, uint16_t* 
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it.  Like the other entry points that return
  * host results, every call copies its result to the host and synchronises
- * `stream`, so it cannot be called on a stream that is being captured into
- * a CUDA graph, nor while another thread holds a global-mode capture.  All
- * calls share the array and each call starts by
+ * `stream`.  All calls share the array and each call starts by
  * clearing what it reads: calls whose work overlaps on the GPU (several
  * streams, several host threads) race on it and must be serialised by the
  * caller.  Device memory only (CD_EINVAL for CD_MEM_HOST); n > 2^20 returns

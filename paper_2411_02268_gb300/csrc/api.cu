@@ -243,6 +243,7 @@ struct Level {
     uint32_t* size = nullptr;
     uint32_t* verts = nullptr;
     uint32_t* movers = nullptr;
+    uint32_t* elab = nullptr;       // MG sweeps with k <= 16: per-entry labels of the first scan
     const uint32_t* cid = nullptr;  // colour id of every vertex (null: the vertex id)
     bool reuse = false;   // prepare_level keeps the buffers of an earlier call (schedule trials)
     uint32_t *tc = nullptr, *to = nullptr;  // bucketing scratch
@@ -302,6 +303,7 @@ int prepare_level(Level& L, const uint32_t* labels, uint32_t* labels_out_copy, i
         CD_TRY(sc.get(&L.Sigma, L.n));
         CD_TRY(sc.get(&L.size, L.n));
         CD_TRY(sc.get(&L.verts, L.n));
+        if (k > 0 && k <= 16) CD_TRY(sc.get(&L.elab, L.nnz));
     }
     L.bt = exact ? exact_table() : table_from(sched);
     L.bt.qmul = slot_lanes(k);
@@ -348,6 +350,7 @@ SweepArgs make_args(const Level& L, const uint32_t* labels_in, uint32_t* labels_
     a.off = L.off; a.cols = L.cols; a.w = L.w;
     a.labels = labels_in; a.K = L.K; a.Sigma = L.Sigma; a.size = L.size;
     a.active = active; a.bound = bound; a.labels_out = labels_out; a.movers = L.movers;
+    a.elab = L.elab;
     a.glob = dglob; a.verts = L.verts; a.n = L.n; a.nnz = L.nnz; a.mode = mode; a.uncond = uncond;
     a.colors = colors; a.sub_color = sub_color;
     a.one_scan = 0;

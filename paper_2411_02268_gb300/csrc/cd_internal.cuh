@@ -90,6 +90,8 @@ struct SweepArgs {
     int colors;               // colour classes of the driver (1: a fully synchronous sweep)
     int sub_color;            // colour class deciding in this sub-sweep
     const uint32_t* cid;      // colour id of every vertex (its id inside its graph); null = the vertex id
+    uint32_t* elab;           // k <= 16: label of every CSR entry as the first scan saw it (kEmpty =
+                              // skipped), read back by the second scan; null = re-gather
     BucketTable bt;
 };
 

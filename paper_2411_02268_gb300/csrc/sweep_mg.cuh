@@ -210,7 +210,7 @@ __device__ __forceinline__ Chunk load_chunk(const SweepArgs& a, int64_t ch) {
 // (in refine mode only for neighbours inside the vertex's bound), in order.
 // Two copies of f per chunk: entries 0 and 1, then 2 and 3 shifted down
 // (four copies cost registers, one copy costs shifts; two measured fastest).
-template <typename F>
+template <bool kSave = false, typename F>
 __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, int64_t c1, int step,
                                             int64_t start, int64_t end, uint32_t i, uint32_t bi, F&& f) {
     const uint32_t len = (uint32_t)(end - start);
@@ -233,6 +233,19 @@ __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, i
             for (int u = 0; u < 4; ++u)
                 if (ok[u]) ok[u] = __ldg(a.bound + cur.c[u]) == bi;
         }
+        if (kSave && a.elab) {
+            // the row's entries of this chunk as the second scan will read them
+            const uint32_t l0 = ok[0] ? labs[0] : kEmpty, l1 = ok[1] ? labs[1] : kEmpty;
+            const uint32_t l2 = ok[2] ? labs[2] : kEmpty, l3 = ok[3] ? labs[3] : kEmpty;
+            if (rel < len && rel + 3u < len && rel + 3u > rel) {
+                reinterpret_cast<uint4*>(a.elab)[ch] = make_uint4(l0, l1, l2, l3);
+            } else {
+                const uint32_t lv[4] = {l0, l1, l2, l3};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (rel + (uint32_t)u < len) a.elab[ch * 4 + u] = lv[u];
+            }
+        }
 #pragma unroll 1
         for (int u = 0; u < 2; ++u) {
             if (ok[0]) f(labs[0], cur.w[0]);
@@ -241,6 +254,36 @@ __device__ __forceinline__ void scan_chunks(const SweepArgs& a, int64_t first, i
             labs[0] = labs[2]; labs[1] = labs[3];
             cur.w[0] = cur.w[2]; cur.w[1] = cur.w[3];
         }
+    }
+}
+
+// The second scan over the labels saved by the first (a.elab): the same
+// chunks, no column loads and no label gathers; f(label, w) for the row's
+// entries the first scan took.
+template <typename F>
+__device__ __forceinline__ void scan_saved(const SweepArgs& a, int64_t first, int64_t c1, int step, int64_t start,
+                                           int64_t end, F&& f) {
+    const uint32_t len = (uint32_t)(end - start);
+    for (int64_t ch = first; ch < c1; ch += step) {
+        const int64_t e0 = ch * 4;
+        const uint32_t rel = (uint32_t)(e0 - start);
+        uint32_t lv[4], wv[4];
+        if (e0 + 4 <= a.nnz) {
+            const uint4 l4 = reinterpret_cast<const uint4*>(a.elab)[ch];
+            const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(a.w) + ch);
+            lv[0] = l4.x; lv[1] = l4.y; lv[2] = l4.z; lv[3] = l4.w;
+            wv[0] = w4.x; wv[1] = w4.y; wv[2] = w4.z; wv[3] = w4.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = e0 + u < a.nnz;
+                lv[u] = in ? a.elab[e0 + u] : kEmpty;
+                wv[u] = in ? a.w[e0 + u] : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (rel + (uint32_t)u < len && lv[u] != kEmpty) f(lv[u], wv[u]);
     }
 }
 
@@ -375,9 +418,9 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
     const int64_t first = c0 + (int64_t)((lane - (int)(c0 & (G - 1))) & (G - 1));
     if (act) {
         if (G == 1) {
-            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+            scan_chunks<true>(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
         } else {
-            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+            scan_chunks<true>(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
         }
     }
     group_merge<G, K, VT>(sk, lane, gmask, unc);
@@ -419,10 +462,12 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
         }
         __syncwarp(gmask);
         if (act) {
-            scan_chunks(a, first, c1, G, start, end, i, bi, [&](uint32_t c, uint32_t w) {
+            auto addt = [&](uint32_t c, uint32_t w) {
                 const int h = tab_find(tk, c);
                 if (h >= 0) atomicAdd(&tv[h], (VT)w);
-            });
+            };
+            if (a.elab) scan_saved(a, first, c1, G, start, end, addt);
+            else scan_chunks(a, first, c1, G, start, end, i, bi, addt);
         }
         __syncwarp(gmask);
         if (lane == 0) {
@@ -446,7 +491,8 @@ __device__ __forceinline__ Outcome group_body(const SweepArgs& a, int64_t vi, bo
 #pragma unroll
                 for (int p = 0; p < K; ++p) acc[p] += c == cand[p] ? (VT)w : (VT)0;
             };
-            scan_chunks(a, first, c1, G, start, end, i, bi, add);
+            if (a.elab) scan_saved(a, first, c1, G, start, end, add);
+            else scan_chunks(a, first, c1, G, start, end, i, bi, add);
         }
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) {
@@ -556,7 +602,7 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
     const int64_t c0 = start >> 2, c1 = (end + 3) >> 2;
     const int64_t first = c0 + (int64_t)((s - (int)(c0 & (L - 1))) & (L - 1));
     if (act) {
-        scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
+        scan_chunks<true>(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) { sk.update(c, (VT)w, unc); });
     }
     block_merge<L, K, VT, U>(sk, s, sb, bar, sm, unc);
     if (wl == 0 && lane == 0) {
@@ -586,11 +632,13 @@ __device__ __forceinline__ Outcome block_body(const SweepArgs& a, int64_t vi, bo
         for (int p = 0; p < K; ++p) acc[p] = 0;
         kid = 0;
         if (act) {
-            scan_chunks(a, first, c1, L, start, end, i, bi, [&](uint32_t c, uint32_t w) {
+            auto addb = [&](uint32_t c, uint32_t w) {
                 kid += c == d ? (VT)w : (VT)0;
 #pragma unroll
                 for (int p = 0; p < K; ++p) acc[p] += c == cand[p] ? (VT)w : (VT)0;
-            });
+            };
+            if (a.elab) scan_saved(a, first, c1, L, start, end, addb);
+            else scan_chunks(a, first, c1, L, start, end, i, bi, addb);
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
