@@ -27,6 +27,11 @@
  *   modularity) synchronise the stream before returning.
  * Scratch: device scratch is allocated with cudaMallocAsync on the stream and
  *   freed before the call returns; its peak size is in cd_last_stats().
+ *   The library raises the release threshold of the device's default memory
+ *   pool (for this process) so that freed scratch stays mapped for the next
+ *   call: to at least 16 GiB and twice the largest scratch of one call, at
+ *   most a quarter of the device's memory.  A caller that needs that memory
+ *   back trims the pool (cudaMemPoolTrimTo on cudaDeviceGetDefaultMemPool).
  *   Fault injection (for tests of callers' error paths): when the
  *   environment variable CD_FAIL_ALLOC holds n >= 1, the n-th scratch
  *   allocation of every call fails with CD_ENOMEM on the host, before the

@@ -48,23 +48,44 @@ int cuda_fail(cudaError_t e) {
         if (_rc != CD_OK) return _rc; \
     } while (0)
 
-// The device's default memory pool (which cudaMallocAsync draws from) keeps up
-// to kPoolKeep bytes of freed scratch between calls instead of returning it
-// to the driver at every synchronisation: calls that allocate the same
-// scratch again (every sweep of a benchmark, every host-memory call) then
-// reuse mapped memory.  Set once per device, for this process only.
+// The device's default memory pool (which cudaMallocAsync draws from) keeps
+// freed scratch between calls instead of returning it to the driver at every
+// synchronisation: calls that allocate the same scratch again (every sweep of
+// a benchmark, every host-memory call) then reuse mapped memory instead of
+// mapping it anew (mapping several GB costs tens of milliseconds).  The pool
+// keeps at least kPoolKeep bytes, and twice the largest scratch of one call
+// seen so far on the device (a pool holding little more than one call's
+// scratch fragments and maps again every few calls), at most a quarter of
+// the device's memory.  Per device, for this process only.
 constexpr uint64_t kPoolKeep = 16ull << 30;
 constexpr int kMaxDevices = 64;
-std::atomic<int> g_pool_set[kMaxDevices];
+std::atomic<uint64_t> g_pool_keep[kMaxDevices];
+
+void set_pool_keep(int dev, uint64_t want) {
+    uint64_t cur = g_pool_keep[dev].load();
+    while (want > cur && !g_pool_keep[dev].compare_exchange_weak(cur, want)) {
+    }
+    if (want <= cur) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+}
 
 void keep_pool_memory() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
-    if (g_pool_set[dev].exchange(1) != 0) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
-    uint64_t keep = kPoolKeep;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (g_pool_keep[dev].load() == 0) set_pool_keep(dev, kPoolKeep);
+}
+
+// After a call: let the pool keep twice this call's scratch (see above).
+void grow_pool_keep(int64_t bytes) {
+    int dev = 0;
+    if (bytes <= 0 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    const uint64_t want = 2ull * (uint64_t)bytes;
+    if (want <= g_pool_keep[dev].load()) return;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return;
+    set_pool_keep(dev, std::min<uint64_t>(want, (uint64_t)total_b / 4));
 }
 
 // Fault injection for tests: with CD_FAIL_ALLOC=n (n >= 1) in the
@@ -89,6 +110,7 @@ struct Scratch {
     ~Scratch() {
         for (void* p : ptrs) cudaFreeAsync(p, s);
         if (bytes > g_stats.scratch_bytes) g_stats.scratch_bytes = bytes;
+        grow_pool_keep(bytes);
     }
     template <typename T>
     int get(T** p, int64_t count_) {
