@@ -114,10 +114,10 @@ __global__ void k_expand(const int64_t* __restrict__ off, const int32_t* __restr
 }
 
 // Stable LSD radix sort pass on 8-bit digits of key (shift), carrying two
-// payload arrays.  Tiles of 8192 entries; digit counts per tile are scanned in
+// payload arrays.  Tiles of 4096 entries; digit counts per tile are scanned in
 // digit-major order so that equal digits keep their tile order.
 constexpr int kRadixThreads = 256;
-constexpr int kRadixRounds = 32;
+constexpr int kRadixRounds = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixRounds;
 
 int64_t radix_tiles(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
@@ -140,24 +140,26 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int sh
 // (digit, then original order), then written out so that consecutive threads
 // write consecutive positions of one digit's run: the global writes coalesce
 // (placing every entry straight at its global position scattered 4 bytes per
-// 32-byte sector over three arrays).  Each of the 16 warps owns a contiguous
+// 32-byte sector over three arrays).  Each of the 8 warps owns a contiguous
 // slice of 512 entries of the tile, whose keys it loads into registers at
 // once (16 per lane): it counts its digits, a prefix over the warps gives
 // each warp where its entries of every digit start, and the warp then places
 // its slice in order (rank among equal digits of a step, steps in order), so
 // the sort stays stable with four block-wide barriers per tile.  The tile's
 // digit counts and output starts come from the scanned histogram
-// (consecutive exclusive offsets in digit-major order).  Two 512-thread
-// blocks per SM (106 KB of shared memory each): the loads are latency-bound,
-// and 32 warps per SM measured faster than 16 warps holding twice the keys.
+// (consecutive exclusive offsets in digit-major order).  Four 256-thread
+// blocks per SM (54 KB of shared memory each): the loads are latency-bound;
+// 32 warps per SM measured faster than 16 warps holding twice the keys, and
+// four small blocks a little faster than two 512-thread blocks on
+// 8192-entry tiles (their barriers overlap).
 constexpr int kRadixSmem = 3 * kRadixTile * (int)sizeof(uint32_t);
-constexpr int kScatterThreads = 512;
+constexpr int kScatterThreads = 256;
 constexpr int kRadixWarps = kScatterThreads / 32;
 constexpr int kRadixSlice = kRadixTile / kRadixWarps;  // entries per warp
 constexpr int kSteps = kRadixSlice / 32;                // keys per lane, held in registers
 constexpr int kBatch = 4;                               // payload loads in flight per lane
 
-__global__ void __launch_bounds__(kScatterThreads, 2) k_radix_scatter(
+__global__ void __launch_bounds__(kScatterThreads, 4) k_radix_scatter(
     const uint32_t* __restrict__ key, const uint32_t* __restrict__ p1, const uint32_t* __restrict__ p2, int64_t n,
     int shift, const uint32_t* __restrict__ offs, int64_t ntiles, uint32_t* __restrict__ key_o,
     uint32_t* __restrict__ p1_o, uint32_t* __restrict__ p2_o) {
