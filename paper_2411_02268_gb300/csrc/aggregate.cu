@@ -12,6 +12,7 @@
 
 #include "cd_internal.cuh"
 #include "csr_walk.cuh"
+#include "warp_vote.cuh"
 
 namespace cdk {
 
@@ -154,19 +155,6 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int sh
 // 8192-entry tiles (their barriers overlap).
 constexpr int kRadixSmem = 3 * kRadixTile * (int)sizeof(uint32_t);
 
-// Lanes of the warp whose 8-bit digit equals this lane's, valid lanes only
-// (invalid lanes form a group of their own): nine votes, one per bit of the
-// digit and one for validity, instead of a match instruction.
-__device__ __forceinline__ unsigned digit_peers(bool ok, int dgt) {
-    const unsigned code = ok ? (unsigned)dgt : 0x100u;
-    unsigned peers = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < 9; ++b) {
-        const unsigned bal = __ballot_sync(0xffffffffu, (code >> b) & 1u);
-        peers &= ((code >> b) & 1u) ? bal : ~bal;
-    }
-    return peers;
-}
 constexpr int kScatterThreads = 256;
 constexpr int kRadixWarps = kScatterThreads / 32;
 constexpr int kRadixSlice = kRadixTile / kRadixWarps;  // entries per warp
@@ -228,7 +216,7 @@ __global__ void __launch_bounds__(kScatterThreads, 4) k_radix_scatter(
     for (int t = 0; t < kSteps; ++t) {
         const bool ok = j0 + t * 32 + lane < tn;
         const int dgt = ok ? (int)((kr[t] >> shift) & 255u) : -1;
-        const unsigned peers = digit_peers(ok, dgt);
+        const unsigned peers = byte_peers(ok, (unsigned)dgt);
         if (ok && (peers & ((1u << lane) - 1u)) == 0) wcnt[warp][dgt] += (uint16_t)__popc(peers);
         __syncwarp();
     }
@@ -260,7 +248,7 @@ __global__ void __launch_bounds__(kScatterThreads, 4) k_radix_scatter(
             const bool ok = j0 + t * 32 + lane < tn;
             const uint32_t k = kr[t];
             const int dgt = ok ? (int)((k >> shift) & 255u) : -1;
-            const unsigned peers = digit_peers(ok, dgt);
+            const unsigned peers = byte_peers(ok, (unsigned)dgt);
             const unsigned below = peers & ((1u << lane) - 1u);
             if (ok) {
                 const uint32_t pos = wcnt[warp][dgt] + __popc(below);

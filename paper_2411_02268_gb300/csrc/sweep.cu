@@ -74,10 +74,15 @@ cudaError_t launch_degrees(const int64_t* off, const uint32_t* w, int64_t n, int
 __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned long long* __restrict__ K,
                          int64_t n, unsigned long long* __restrict__ Sigma, uint32_t* __restrict__ size,
                          Globals* glob) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long k = 0;
-    if (i < n) {
-        k = K[i];
+    // a grid of a few blocks per SM strides over the vertices, so that the
+    // two global atomics per block (2m and max K_i, one address each) stay
+    // few: one block per 256 vertices made them serialise on those
+    // addresses
+    unsigned long long s = 0, m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = K[i];
+        s += k;
+        m = k > m ? k : m;
         if (!labels) {
             // singleton communities (labels = vertex ids): plain stores
             Sigma[i] = k;
@@ -92,10 +97,8 @@ __global__ void k_totals(const uint32_t* __restrict__ labels, const unsigned lon
             }
         }
     }
-    // block reduction, then one atomic per block (a single address would
-    // otherwise serialise one atomic per warp)
+    // block reduction, then one atomic per block
     __shared__ unsigned long long ss[8], sm[8];
-    unsigned long long s = k, m = k;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, o);
@@ -227,9 +230,14 @@ cudaError_t launch_totals(const uint32_t* labels, const uint64_t* K, int64_t n, 
         if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), s);
     }
     if (e != cudaSuccess || n == 0) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (n + 255) / 256, cap = (int64_t)sms * 8;
     note_launch();
-    k_totals<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(labels, (const unsigned long long*)K, n,
-                                                          (unsigned long long*)Sigma, size, glob);
+    k_totals<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(labels, (const unsigned long long*)K, n,
+                                                                  (unsigned long long*)Sigma, size, glob);
     return cudaGetLastError();
 }
 
