@@ -1036,16 +1036,19 @@ int input_level(const cd_csr* g, Scratch& sc, Level* L) {
     return CD_OK;
 }
 
+// Q of labels on the level's graph.  The weighted degrees are the level's
+// own (L.K, left by a local-moving phase on it) when it has them, else they
+// are computed here.
 int modularity_of(const Level& L, const uint32_t* labels, Scratch& sc, Globals* dglob, cudaStream_t s,
                   double* q) {
-    uint64_t *K, *Sig;
+    uint64_t *K = L.K, *Sig;
     uint32_t* sz;
-    CD_TRY(sc.get(&K, L.n));
+    if (!K) CD_TRY(sc.get(&K, L.n));
     CD_TRY(sc.get(&Sig, L.n));
     CD_TRY(sc.get(&sz, L.n));
     CD_CUDA(cudaMemsetAsync(dglob, 0, sizeof(Globals), s));
     if (L.n > 0) {
-        CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, K, dglob, s));
+        if (!L.K) CD_CUDA(launch_degrees(L.off, L.w, L.n, L.nnz, K, dglob, s));
         CD_CUDA(launch_modularity(L.off, L.cols, L.w, labels, L.n, L.nnz, K, Sig, sz, dglob, s));
     }
     HostGlobals hg;
@@ -1375,6 +1378,7 @@ int cd_louvain(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double
         uint32_t* lab;
         int64_t sw = 0;
         CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, nullptr, &lab, &sw));
+        if (pass == 0) in.K = cur.K;  // the input's weighted degrees, for the final Q
         g_stats.sweeps += sw;
         g_stats.passes += 1;
         uint32_t* dense;
@@ -1859,6 +1863,7 @@ int cd_leiden(const cd_csr* g, const cd_params* p, uint32_t* labels_out, double*
         uint32_t* lab;
         int64_t sw = 0;
         CD_TRY(local_move(cur, p, CD_MODE_LOUVAIN, tol, sched, sc, dglob, s, init, &lab, &sw));
+        if (pass == 0) in.K = cur.K;  // the input's weighted degrees, for the final Q
         g_stats.sweeps += sw;
         g_stats.passes += 1;
         uint32_t* dc;
