@@ -347,6 +347,7 @@ int bits_for(int64_t nc) {
 // with ties in input order.  On return the sorted arrays are in (src, dst, w)
 // (the buffers may have been swapped with the *2 ones).
 cudaError_t radix_sort_keys(AggScratch& a, int64_t nnz, int bits_src, int bits_dst, Globals* glob, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;  // nothing to order (and no tile to launch)
     {
         cudaError_t e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kRadixSmem);
         if (e != cudaSuccess) return e;

@@ -50,6 +50,19 @@ def test_aggregate_matches_oracle(env, gname):
         assert np.array_equal(G2.weights.cpu().numpy().view(np.uint32), R2.w)
 
 
+def test_aggregate_edgeless_graph(env):
+    """A graph without edges aggregates to its communities with no entries
+    (the sort has no tile to run)."""
+    cd, torch = env
+    g = gen.from_edges(5, [], [], [])
+    lab = np.array([0, 1, 1, 2, 0], np.uint32)
+    dense, G2 = cd.cd_aggregate(cd.Graph.to_device(g), torch.from_numpy(lab.view(np.int32)).cuda())
+    R2, rdense = oracle.aggregate(g, lab)
+    assert np.array_equal(dense.cpu().numpy().view(np.uint32), rdense)
+    assert G2.n == R2.n == 3 and G2.nnz == 0
+    assert np.array_equal(G2.offsets.cpu().numpy(), R2.offsets)
+
+
 def test_aggregate_overflow_reported(env):
     cd, torch = env
     big = 2**31
