@@ -145,7 +145,8 @@ typedef struct cd_params {
                              sub-sweep (refine mode: 0 = 8; Louvain mode: 0 = 1, one class) */
     int32_t sub_color;    /* cd_sweep: the colour class deciding in this sweep (pass the
                              vertices of that class as `active`); the rules that guard
-                             against simultaneous moves read it (see cd_sweep) */
+                             against simultaneous moves read it (see cd_sweep).  Must be
+                             below the sweep's number of classes (CD_EINVAL otherwise) */
     int32_t one_scan;     /* LPA only (cd_sweep mode LPA, cd_lpa): the "1-scan" variant of
                              Section 4.3, deciding on the sketch values without the second
                              scan (needs k > 0) */

@@ -1189,7 +1189,9 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     if (mode != CD_MODE_LOUVAIN && mode != CD_MODE_LPA && mode != CD_MODE_REFINE) return CD_EINVAL;
     if ((mode == CD_MODE_REFINE) != (bound != nullptr)) return CD_EINVAL;
     if (p->one_scan && mode != CD_MODE_LPA) return CD_EINVAL;
-    if (p->colors < 0 || p->colors > 16 || p->sub_color < 0 || p->sub_color >= resolve_colors(p)) return CD_EINVAL;
+    // colour classes of this sweep: refine mode defaults to 8, the others to 1
+    const int ncol = mode == CD_MODE_REFINE ? resolve_colors(p) : (p->colors == 0 ? 1 : p->colors);
+    if (p->colors < 0 || p->colors > 16 || p->sub_color < 0 || p->sub_color >= ncol) return CD_EINVAL;
     if (!labels_in || !labels_out || labels_in == labels_out) return CD_EINVAL;
     cudaStream_t s = (cudaStream_t)p->stream;
     cd_schedule sched;
@@ -1264,7 +1266,6 @@ int cd_sweep(const cd_csr* g, const cd_params* p, int mode, const uint32_t* labe
     if (host) CD_CUDA(cudaStreamWaitEvent(s, side.ev[2], 0));  // the columns before the sweep
     // refine: the driver's colour classes (0 = 8); Louvain: the singleton
     // rule's classes (0 = one class, every vertex decides together)
-    const int ncol = mode == CD_MODE_REFINE ? resolve_colors(p) : (p->colors == 0 ? 1 : p->colors);
     SweepArgs a = make_args(L, lin, lout, act, bound, dglob, mode, p->subtract, ncol, p->sub_color);
     a.one_scan = p->one_scan;
     Timer tm;

@@ -103,6 +103,13 @@ def test_argument_checks_without_gpu(cd):
     assert rc(cd.make_params(k=8, one_scan=True), mode=cd.MODE_LOUVAIN) == cd.CD_EINVAL
     assert rc(cd.make_params(k=0, one_scan=True), mode=cd.MODE_LPA) == cd.CD_EINVAL
     assert rc(cd.make_params(k=8), mode=cd.MODE_REFINE) == cd.CD_EINVAL   # refine needs a bound
+    assert rc(cd.make_params(k=8, colors=0, sub_color=1)) == cd.CD_EINVAL  # one class in Louvain mode
+    assert rc(cd.make_params(k=8, colors=4, sub_color=4)) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=8, colors=17)) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=16, subtract=2)) == cd.CD_EINVAL           # textbook summary: k <= 8
+    assert rc(cd.make_params(k=8, agg_k=3)) == cd.CD_EINVAL
+    assert rc(cd.make_params(k=8, skip_rule=1)) == cd.CD_EINVAL           # the learned rule needs a model
+    assert rc(cd.make_params(k=8, schedule=cd.schedule_from([10**9], [8], blocks_per_sm=9))) == cd.CD_EINVAL
     bad_sched = cd.schedule_from([4, 2], [1, 2])
     assert rc(cd.make_params(k=8, schedule=bad_sched)) == cd.CD_EINVAL
     bad_sched = cd.schedule_from([4, 10**9], [1, 3])
